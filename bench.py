@@ -1,0 +1,321 @@
+"""Benchmark of the algebraic-distance sparsification hot path on one GB300.
+
+Workload (a "step"): R-MAT scale 20 (1,048,576 vertices, edge factor 16,
+a/b/c/d = 0.57/0.19/0.19/0.05, symmetrised, no self loops or duplicates, unit
+weights), R = 32 Philox test vectors, k = 20 JOR sweeps at omega = 0.5 with a
+rescale after every sweep, the per-edge distance, then Alg. 2 sparsification
+to 30% of the edges per node in local and in global mode.  Inputs are
+resident in device memory when the timed region starts.
+
+Metric: edge-vector updates per second = nnz * R * k / step time (nnz counts
+both CSR directions).  Also reported: the end-to-end figure through the C ABI
+with host buffers (graph upload and result download inside the timed region),
+the HBM roofline fraction of the dominant kernel (one JOR sweep), and the FP64
+oracle timed on the host cores on a bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|bf16]
+    python bench.py --impl reference      # the FP64 CPU oracle, same metric
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "JOR+distance edge-vector updates/s (nnz*R*k/s) & % HBM roofline vs FP32 plain"
+UNIT = "edge-vector updates/s"
+R, K_SWEEPS, OMEGA, SEED, FRACTION = 32, 20, 0.5, 0x1601055270000000, 0.30
+SCALE, EDGE_FACTOR, GRAPH_SEED = 20, 16, 2
+WORKLOAD = (f"R-MAT scale {SCALE} (2^{SCALE} vertices, edge factor {EDGE_FACTOR}, a=0.57 b=0.19 c=0.19 d=0.05, "
+            f"symmetrised, dedup, unit weights), R={R}, k={K_SWEEPS}, omega={OMEGA}, per-sweep rescale, "
+            f"L2 distance, per-node sparsification to {int(FRACTION * 100)}% local and global")
+
+
+def sweep_source_digest() -> str:
+    p = os.path.join(ROOT, "paper_1601_05527_gb300", "csrc", "sweep.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sweep_traffic(storage):
+    """DRAM bytes per sweep launch from the committed ncu summary, if the
+    sweep kernel source is unchanged since it was captured."""
+    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(storage)
+    if not e or e.get("sweep_cu_sha256_16") != sweep_source_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 7:
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                except ValueError:
+                    pass
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_graph():
+    from paper_1601_05527_gb300 import graphgen
+    return graphgen.rmat(SCALE, EDGE_FACTOR, seed=GRAPH_SEED)
+
+
+def algorithmic_bytes_per_sweep(g, storage):
+    """Compulsory traffic of one sweep (gathers assumed served on chip): column
+    indices, row pointers, inverse degrees, and one read + one write of every
+    active row of the R-wide vector block."""
+    s = 2 if storage == "bf16" else 4
+    n_active = int((g.degrees() > 0).sum())
+    return g.nnz * 4 + (g.n + 1) * 4 + g.n * 4 + 2 * n_active * R * s, n_active
+
+
+def cpu_baseline(g, budget_s=20.0):
+    """The FP64 oracle as it stands (single-threaded C) on a bounded sample:
+    the full graph with R = 32 test vectors and one JOR sweep."""
+    import oracle
+    k = 1
+    t0 = time.perf_counter()
+    oracle.algebraic_distance(g.row_ptr, g.col, None, R=R, k=k, omega=OMEGA, seed=SEED)
+    dt = time.perf_counter() - t0
+    return {"value": g.nnz * R * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"same R-MAT scale-{SCALE} graph, R={R}, k={k} sweep (+ init and distance), FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    g = make_graph()
+    import oracle
+    oracle.build()
+    k = 1
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.algebraic_distance(g.row_ptr, g.col, None, R=R, k=k, omega=OMEGA, seed=SEED)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    value = args.steps * g.nnz * R * k / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"each step: FP64 oracle, R={R}, k={k} sweep on the full graph",
+                       "n": g.n, "m": g.m, "nnz": g.nnz},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"R={R}, k={k} sweep (+ init and distance) on the full graph per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1601_05527_gb300 import build, _lib as L
+    build.build()
+    L.load()
+    L.use_torch_allocator()
+    g = make_graph()
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+    rp_d = torch.from_numpy(g.row_ptr).to(dev)
+    col_d = torch.from_numpy(g.col).to(dev)
+    h = L.ad_graph_create(g.n, rp_d, col_d, None, 0, stream)
+    keep_d = torch.empty(g.m, dtype=torch.uint8, device=dev)
+    storage = args.storage
+
+    def step(handle, keep):
+        L.ad_algebraic_distance(handle, R, K_SWEEPS, OMEGA, SEED, 0, storage, 0, None)
+        kl, el = L.ad_sparsify(handle, FRACTION, "local", "per_node", keep)
+        kg, eg = L.ad_sparsify(handle, FRACTION, "global", "per_node", keep)
+        return kl, kg
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step(h, keep_d)
+    clocks = Clocks()
+    clocks.start()
+    barrier()
+    launches0 = L.ad_kernel_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    kept = None
+    for _ in range(args.steps):
+        kept = step(h, keep_d)
+    ev1.record(stream)
+    barrier()
+    launches = L.ad_kernel_launch_count() - launches0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms)
+    units = g.nnz * R * K_SWEEPS
+    value = ws * args.steps * units / (ms / 1e3)
+
+    # phase split and the dominant kernel's launch time (events on the handle's stream)
+    L.ad_graph_set_profiling(h, True)
+    for ph in ("init", "sweep", "distance", "select"):
+        L.ad_graph_phase_time(h, ph, reset=True)
+    prof_steps = 2
+    for _ in range(prof_steps):
+        step(h, keep_d)
+    phase = {ph: L.ad_graph_phase_time(h, ph) for ph in ("init", "sweep", "distance", "select")}
+    L.ad_graph_set_profiling(h, False)
+    sweep_ms = phase["sweep"][0] / max(phase["sweep"][1], 1)
+    b_sweep, n_active = algorithmic_bytes_per_sweep(g, storage)
+    peak, peak_kind = measured_peaks()
+    achieved = b_sweep / (sweep_ms / 1e3) / 1e9
+    jd_ms = (phase["init"][0] + phase["sweep"][0] + phase["distance"][0]) / prof_steps
+
+    # end to end through the C ABI with host buffers (pinned), upload and download timed
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    keep_h = torch.empty(g.m, dtype=torch.uint8).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        he = L.ad_graph_create(g.n, rp_h, col_h, None, 0, stream)
+        L.ad_algebraic_distance(he, R, K_SWEEPS, OMEGA, SEED, 0, storage, 0, None)
+        L.ad_sparsify(he, FRACTION, "local", "per_node", keep_h)
+        L.ad_sparsify(he, FRACTION, "global", "per_node", keep_h)
+        L.ad_graph_destroy(he)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = ws * e2e_steps * units / e2e_s
+    h2d = rp_h.numel() * 8 + col_h.numel() * 4
+    d2h = 2 * g.m
+
+    L.ad_graph_destroy(h)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if storage == "fp32" else "bf16 storage, f32 accumulate",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": g.n, "n_active": n_active, "m": g.m, "nnz": g.nnz,
+                           "R": R, "k": K_SWEEPS, "storage": storage, "graph_digest": g.digest(),
+                           "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "l2": "no flush: per-sweep traffic (column indices 126 MB + vector block) exceeds the 129 MB L2"},
+                "phases_ms_per_step": {"init": phase["init"][0] / prof_steps, "sweeps": phase["sweep"][0] / prof_steps,
+                                       "distance": phase["distance"][0] / prof_steps,
+                                       "select_local_and_global": phase["select"][0] / prof_steps},
+                "jor_distance_only": {"value": units / (jd_ms / 1e3), "unit": UNIT, "ms": jd_ms},
+                "sparsify_kept": {"local": kept[0] if kept else None, "global": kept[1] if kept else None},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "steps": e2e_steps},
+                "roofline": {"kernel": "k_sweep (one JOR sweep + fused rescale min/max)", "bound": "hbm",
+                             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": b_sweep,
+                             "avg_launch_ms": sweep_ms, "traffic": sweep_traffic(storage)},
+                "gpu_launches": int(launches),
+                "clocks": clk}
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(g)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    return run_reference(args) if args.impl == "reference" else run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

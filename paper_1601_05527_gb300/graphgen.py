@@ -71,25 +71,46 @@ def from_edges(n: int, u, v, edge_weight=None, name: str = "") -> Graph:
     u = np.asarray(u, dtype=np.int64)
     v = np.asarray(v, dtype=np.int64)
     keep = u != v
-    u, v = u[keep], v[keep]
-    a, b = np.minimum(u, v), np.maximum(u, v)
+    a, b = np.minimum(u[keep], v[keep]), np.maximum(u[keep], v[keep])
     key = a * np.int64(n) + b
-    key, first = np.unique(key, return_index=True)
-    a = key // n
-    b = key % n
     w = None
     if edge_weight is not None:
-        w = np.asarray(edge_weight, dtype=np.float32)[keep][first]
-    rows = np.concatenate([a, b])
-    cols = np.concatenate([b, a])
-    order = np.lexsort((cols, rows))
-    rows, cols = rows[order], cols[order]
+        order = np.argsort(key, kind="stable")
+        key = key[order]
+        w = np.asarray(edge_weight, dtype=np.float32)[keep][order]
+    else:
+        key = np.sort(key)
+    first = np.ones(len(key), dtype=bool)
+    first[1:] = key[1:] != key[:-1]
+    key = key[first]
+    if w is not None:
+        w = w[first]
+    # upper pairs (a < b) in (a, b) order = edge-id order
+    a = (key // n).astype(np.int64)
+    b = (key % n).astype(np.int64)
+    m = len(key)
+    cnt_up = np.bincount(a, minlength=n)
+    cnt_lo = np.bincount(b, minlength=n)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(np.bincount(rows, minlength=n), out=row_ptr[1:])
+    np.cumsum(cnt_up + cnt_lo, out=row_ptr[1:])
+    col = np.empty(2 * m, dtype=np.int32)
+    # row i = its lower entries (columns a < i, in a order) then its upper entries (b > i)
+    lo_order = np.argsort(b, kind="stable")
+    lo_start = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt_lo, out=lo_start[1:])
+    bl = b[lo_order]
+    pos_lo = row_ptr[bl] + (np.arange(m, dtype=np.int64) - lo_start[bl])
+    col[pos_lo] = a[lo_order]
+    up_start = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt_up, out=up_start[1:])
+    pos_up = row_ptr[a] + cnt_lo[a] + (np.arange(m, dtype=np.int64) - up_start[a])
+    col[pos_up] = b
     weight = None
     if w is not None:
-        weight = np.concatenate([w, w])[order].astype(np.float32)
-    return Graph(n=n, row_ptr=row_ptr, col=cols.astype(np.int32), weight=weight, name=name)
+        weight = np.empty(2 * m, dtype=np.float32)
+        weight[pos_lo] = w[lo_order]
+        weight[pos_up] = w
+    return Graph(n=n, row_ptr=row_ptr, col=col, weight=weight, name=name)
 
 
 def with_edge_weights(g: Graph, edge_weight) -> Graph:
@@ -123,22 +144,16 @@ def rmat(scale: int, edge_factor: int = 16, a=0.57, b=0.19, c=0.19, seed: int = 
     n = 1 << scale
     E = edge_factor * n
     rng = np.random.default_rng(seed)
-    src = np.zeros(E, dtype=np.int64)
-    dst = np.zeros(E, dtype=np.int64)
-    chunk = 1 << 22
-    ab, abc = a + b, a + b + c
-    for lo in range(0, E, chunk):
-        hi = min(E, lo + chunk)
-        s = np.zeros(hi - lo, dtype=np.int64)
-        d = np.zeros(hi - lo, dtype=np.int64)
-        for _ in range(scale):
-            r = rng.random(hi - lo)
-            sb = (r >= ab).astype(np.int64)                      # quadrants c, d: lower half
-            db = ((r >= a) & (r < ab)) | (r >= abc)               # quadrants b, d: right half
-            s = (s << 1) | sb
-            d = (d << 1) | db.astype(np.int64)
-        src[lo:hi] = s
-        dst[lo:hi] = d
+    src = np.zeros(E, dtype=np.uint32)
+    dst = np.zeros(E, dtype=np.uint32)
+    ab, abc = np.float32(a + b), np.float32(a + b + c)
+    fa = np.float32(a)
+    for _ in range(scale):
+        r = rng.random(E, dtype=np.float32)
+        src <<= 1
+        src |= (r >= ab)                                       # quadrants c, d: lower half
+        dst <<= 1
+        dst |= ((r >= fa) & (r < ab)) | (r >= abc)             # quadrants b, d: right half
     return from_edges(n, src, dst, name=f"rmat{scale}_ef{edge_factor}")
 
 

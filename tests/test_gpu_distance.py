@@ -1,0 +1,182 @@
+"""GPU parity of ComputeAlgDist (Alg. 1): Philox init, JOR sweeps with the
+per-sweep rescale, edge distances, through the C ABI, against the FP64 oracle
+on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_05527_gb300 import graphgen
+from gpu_util import assert_rho_close, entry_weights_f64, lib, rho_error
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_rho(g, R, k, omega, seed, stream_id=0, storage="fp32", normalize=False):
+    L = lib()
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, g.weight)
+    try:
+        rho = np.zeros(g.m, dtype=np.float32)
+        L.ad_algebraic_distance(h, R, k, omega, seed, stream_id, storage, L.AD_DIST_NORMALIZE if normalize else 0,
+                                rho)
+        return rho
+    finally:
+        L.ad_graph_destroy(h)
+
+
+def ref_rho(g, R, k, omega, seed, stream_id=0, normalize=False, x0=None):
+    return oracle.algebraic_distance(g.row_ptr, g.col, entry_weights_f64(g), R=R, k=k, omega=omega, seed=seed,
+                                     stream=stream_id, normalize=normalize, x0=x0)
+
+
+def weighted(g, seed=1):
+    return graphgen.with_edge_weights(g, graphgen.lognormal_edge_weights(g.m, seed=seed))
+
+
+GRAPHS = {
+    "grid64": lambda: graphgen.grid2d(64, 64),
+    "rmat12": lambda: graphgen.rmat(12, 16, seed=3),
+    "rmat11w": lambda: weighted(graphgen.rmat(11, 16, seed=4)),
+    "ba3000": lambda: graphgen.barabasi_albert(3000, 8, seed=5),
+    "ws4000": lambda: graphgen.watts_strogatz(4000, 10, 0.1, seed=6),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_rho_matches_oracle_fp32(name):
+    g = GRAPHS[name]()
+    R, k = (8, 20) if name == "grid64" else (32, 20)
+    rho = gpu_rho(g, R, k, 0.5, seed=0x1601055270000000)
+    assert_rho_close(rho, ref_rho(g, R, k, 0.5, seed=0x1601055270000000))
+
+
+@pytest.mark.parametrize("R", [1, 3, 10, 16, 24, 40, 64, 100, 128, 256])
+def test_ragged_vector_counts(R):
+    g = graphgen.rmat(10, 8, seed=7)
+    assert_rho_close(gpu_rho(g, R, 6, 0.5, seed=R), ref_rho(g, R, 6, 0.5, seed=R))
+
+
+@pytest.mark.parametrize("omega,k", [(0.3, 9), (0.8, 5), (1.0, 4), (0.5, 1), (0.5, 0)])
+def test_damping_and_sweep_counts(omega, k):
+    g = weighted(graphgen.barabasi_albert(2000, 5, seed=8), seed=9)
+    assert_rho_close(gpu_rho(g, 16, k, omega, seed=3, stream_id=5), ref_rho(g, 16, k, omega, seed=3, stream_id=5))
+
+
+def test_init_is_bit_identical_to_oracle():
+    # k = 0: rho of the raw Philox vectors; only FP32 rounding of sum/sqrt remains
+    g = graphgen.rmat(11, 8, seed=1)
+    rho = gpu_rho(g, 32, 0, 0.5, seed=77, stream_id=9)
+    ref = ref_rho(g, 32, 0, 0.5, seed=77, stream_id=9)
+    assert np.max(np.abs(rho - ref) / np.maximum(ref, 1e-30)) < 2e-6
+
+
+def test_normalized_scores():
+    g = weighted(graphgen.rmat(11, 16, seed=2), seed=3)
+    assert_rho_close(gpu_rho(g, 16, 10, 0.5, seed=4, normalize=True), ref_rho(g, 16, 10, 0.5, seed=4, normalize=True))
+
+
+def test_single_edge_components_and_isolated_vertices():
+    u = np.array([0, 2, 4, 6, 6, 7])
+    v = np.array([1, 3, 5, 7, 8, 8])
+    g = graphgen.from_edges(12, u, v)          # vertices 9..11 isolated
+    rho = gpu_rho(g, 8, 4, 0.5, seed=1)
+    assert np.all(rho[:3] == 0.0) and np.all(rho[3:] > 0)
+    g1 = graphgen.from_edges(2, [0], [1])
+    r1 = gpu_rho(g1, 8, 3, 0.3, seed=1)
+    np.testing.assert_allclose(r1, np.sqrt(8), rtol=1e-6)
+
+
+def test_isolated_vertices_do_not_change_distances():
+    g = graphgen.rmat(10, 8, seed=3)
+    eu, ev = g.edges_upper()
+    g2 = graphgen.from_edges(g.n + 500, eu, ev)
+    np.testing.assert_array_equal(gpu_rho(g, 16, 8, 0.5, seed=2), gpu_rho(g2, 16, 8, 0.5, seed=2))
+
+
+def test_deterministic():
+    g = graphgen.rmat(12, 16, seed=3)
+    a = gpu_rho(g, 32, 10, 0.5, seed=5)
+    b = gpu_rho(g, 32, 10, 0.5, seed=5)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_empty_and_edgeless_graphs():
+    L = lib()
+    for n in (0, 7):
+        h = L.ad_graph_create(n, np.zeros(n + 1, np.int64), np.zeros(0, np.int32))
+        info = L.ad_graph_info(h)
+        assert info["m"] == 0 and info["n_active"] == 0
+        L.ad_algebraic_distance(h, 8, 5, 0.5, 1, 0, "fp32", 0, np.zeros(0, np.float32))
+        keep = np.zeros(0, np.uint8)
+        assert L.ad_sparsify(h, 0.5, "local", "whole_graph", keep)[0] == 0
+        assert L.ad_sparsify(h, 0.5, "global", "per_node", keep)[0] == 0
+        L.ad_graph_destroy(h)
+
+
+def test_bf16_storage_error_against_fp64():
+    g = graphgen.rmat(12, 16, seed=3)
+    ref = ref_rho(g, 32, 20, 0.5, seed=11)
+    err = rho_error(gpu_rho(g, 32, 20, 0.5, seed=11, storage="bf16"), ref)
+    # BF16 keeps 8 significant bits per stored value; the error is reported, not held to FP32 tolerance
+    assert err < 0.1, err
+
+
+def test_torch_device_tensors_in_and_out():
+    import torch
+    L = lib()
+    g = graphgen.rmat(10, 8, seed=3)
+    dev = torch.device("cuda")
+    h = L.ad_graph_create(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev), None)
+    out = torch.zeros(g.m, dtype=torch.float32, device=dev)
+    L.ad_algebraic_distance(h, 16, 5, 0.5, 3, 0, "fp32", 0, out)
+    torch.cuda.synchronize()
+    L.ad_graph_destroy(h)
+    np.testing.assert_array_equal(out.cpu().numpy(), gpu_rho(g, 16, 5, 0.5, seed=3))
+
+
+@pytest.mark.parametrize("bad", ["asym", "self", "dup", "unsorted", "negw", "nanw", "asymw", "range", "rowptr"])
+def test_invalid_graphs_are_rejected(bad):
+    L = lib()
+    g = graphgen.grid2d(3, 3)
+    rp, col = g.row_ptr.copy(), g.col.copy()
+    w = np.ones(g.nnz, np.float32)
+    expect = {"asym": 2, "self": 3, "dup": 4, "unsorted": 4, "negw": 5, "nanw": 5, "asymw": 2, "range": 10,
+              "rowptr": 10}[bad]
+    if bad == "asym":
+        col[1] = 5 if col[1] != 5 else 7          # row 0 gets an entry without its mirror
+        col[:2] = np.sort(col[:2])
+    elif bad == "self":
+        col[0] = 0
+    elif bad in ("dup", "unsorted"):
+        col[1] = col[0] if bad == "dup" else col[1]
+        if bad == "unsorted":
+            col[0], col[1] = col[1], col[0]
+    elif bad == "negw":
+        w[3] = -1.0
+    elif bad == "nanw":
+        w[3] = np.nan
+    elif bad == "asymw":
+        w[0] = 2.0
+    elif bad == "range":
+        col[-1] = 99
+    elif bad == "rowptr":
+        rp[4] = rp[3] - 1
+    with pytest.raises(L.ADError) as ei:
+        L.ad_graph_create(g.n, rp, col, w)
+    assert ei.value.status == expect, (bad, ei.value)
+
+
+def test_edge_across_batch_is_rejected():
+    L = lib()
+    g = graphgen.from_edges(6, [0, 1, 3, 2], [1, 2, 4, 3])     # edge (2,3) joins the two graphs
+    with pytest.raises(L.ADError) as ei:
+        L.ad_graph_create_batched([0, 3, 6], g.n, g.row_ptr, g.col)
+    assert ei.value.status == 1
+
+
+def test_full_size_rmat20_parity_two_sweeps():
+    """The workload of the benchmark (R-MAT scale 20, R = 32, FP32) at k = 2 sweeps,
+    compared on every edge; the oracle needs about half a minute."""
+    g = graphgen.rmat(20, 16, seed=2)
+    rho = gpu_rho(g, 32, 2, 0.5, seed=0x1601055270000000)
+    ref = ref_rho(g, 32, 2, 0.5, seed=0x1601055270000000)
+    assert_rho_close(rho, ref)
