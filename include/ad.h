@@ -68,10 +68,18 @@ typedef enum {
     AD_SCOPE_WHOLE_GRAPH = 1    /* one ranking of all edges (the global-threshold filtering of Sec. 1.1) */
 } ad_scope;
 
-/* Storage type of the R test vectors; sweeps always accumulate in FP32. */
+/*
+ * Storage type of the R test vectors between sweeps; sweeps always
+ * accumulate in FP32.  Every stored iterate lies in [-1/2, 1/2] (a sweep
+ * output is a convex combination of rescaled values), so besides IEEE
+ * formats a 16-bit fixed-point code with step 2^-16 is offered: the same
+ * bytes as BF16/FP16 with a uniform absolute error <= 2^-17.
+ */
 typedef enum {
     AD_STORAGE_FP32 = 0,
-    AD_STORAGE_BF16 = 1
+    AD_STORAGE_BF16 = 1,
+    AD_STORAGE_FP16 = 2,
+    AD_STORAGE_Q16 = 3          /* int16 q, value q * 2^-16 */
 } ad_storage;
 
 /* ad_graph_create flags */
@@ -165,6 +173,14 @@ ad_status ad_graph_destroy(ad_graph_t g);
 /* Sizes: vertices, undirected edges, CSR entries, vertices of degree > 0, graphs in the batch. */
 ad_status ad_graph_info(ad_graph_t g, int64_t *n, int64_t *m, int64_t *nnz, int64_t *n_active,
                         int32_t *n_graphs);
+
+/*
+ * Copy the handle's CSR into caller arrays: row_ptr[n+1], col[nnz] and, when
+ * the graph has explicit weights, weight[nnz] (each may be NULL to skip; host
+ * or device memory).  *has_weight (may be NULL) is set to 0 for unit weights,
+ * in which case weight is left untouched.  Used to read coarse graphs.
+ */
+ad_status ad_graph_export(ad_graph_t g, int64_t *row_ptr, int32_t *col, float *weight, int32_t *has_weight);
 
 /* First edge id of each graph of a batch: edge_offset[n_graphs + 1] (host array). */
 ad_status ad_graph_edge_offsets(ad_graph_t g, int64_t *edge_offset);
@@ -276,7 +292,10 @@ typedef struct {
  * Eq. (P) (an F vertex joins its seed neighbour of smallest rho, ties to the
  * smaller seed id; coarse ids number the seeds by vertex id) and the
  * Galerkin coarse graph L_c = P^T L_f P, until n <= coarsest_n, n_c > 0.9
- * n_f, or max_levels.  The handle keeps the hierarchy; g must outlive it.
+ * n_f, or max_levels.  The handle keeps the hierarchy; g must outlive it,
+ * and the scores kept in g are replaced by the level-0 distances.
+ * Errors: AD_ERR_INVALID_ARG (bad parameters, Q outside [0, 1), a batch),
+ * AD_ERR_OOM, AD_ERR_CUDA.
  */
 ad_status ad_ml_build(ad_graph_t g, const ad_ml_params *params, ad_ml_t *out);
 

@@ -23,14 +23,14 @@ STATUS = {0: "AD_OK", 1: "AD_ERR_INVALID_ARG", 2: "AD_ERR_NOT_SYMMETRIC", 3: "AD
           8: "AD_ERR_TIMEOUT", 9: "AD_ERR_STATE", 10: "AD_ERR_BAD_CSR"}
 AD_MODE_LOCAL, AD_MODE_GLOBAL = 0, 1
 AD_SCOPE_PER_NODE, AD_SCOPE_WHOLE_GRAPH = 0, 1
-AD_STORAGE_FP32, AD_STORAGE_BF16 = 0, 1
+AD_STORAGE_FP32, AD_STORAGE_BF16, AD_STORAGE_FP16, AD_STORAGE_Q16 = 0, 1, 2, 3
 AD_CREATE_SKIP_VALIDATION = 0x1
 AD_DIST_NORMALIZE = 0x1
 AD_DIST_KEEP_STATE = 0x2
 
 MODES = {"local": AD_MODE_LOCAL, "global": AD_MODE_GLOBAL}
 SCOPES = {"per_node": AD_SCOPE_PER_NODE, "whole_graph": AD_SCOPE_WHOLE_GRAPH}
-STORAGES = {"fp32": AD_STORAGE_FP32, "bf16": AD_STORAGE_BF16}
+STORAGES = {"fp32": AD_STORAGE_FP32, "bf16": AD_STORAGE_BF16, "fp16": AD_STORAGE_FP16, "q16": AD_STORAGE_Q16}
 
 
 class ADError(RuntimeError):
@@ -64,6 +64,7 @@ _SIGS = {
     "ad_graph_destroy": (ctypes.c_int, [_VP]),
     "ad_graph_info": (ctypes.c_int, [_VP, _PI64, _PI64, _PI64, _PI64, _PI32]),
     "ad_graph_edge_offsets": (ctypes.c_int, [_VP, _VP]),
+    "ad_graph_export": (ctypes.c_int, [_VP, _VP, _VP, _VP, _PI32]),
     "ad_graph_set_edge_weights": (ctypes.c_int, [_VP, _VP]),
     "ad_algebraic_distance": (ctypes.c_int, [_VP, _I32, _I32, _D, _U64, _U32, ctypes.c_int, _I32, _VP]),
     "ad_algebraic_distance_backward": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -240,6 +241,17 @@ def ad_graph_edge_offsets(g):
     out = np.zeros(G + 1, dtype=np.int64)
     _check(load().ad_graph_edge_offsets(g, out.ctypes.data))
     return out
+
+
+def ad_graph_export(g):
+    """(row_ptr int64[n+1], col int32[nnz], weight float32[nnz] or None) of a handle."""
+    info = ad_graph_info(g)
+    rp = np.zeros(info["n"] + 1, np.int64)
+    col = np.zeros(info["nnz"], np.int32)
+    w = np.zeros(info["nnz"], np.float32)
+    hw = ctypes.c_int32()
+    _check(load().ad_graph_export(g, rp.ctypes.data, col.ctypes.data, w.ctypes.data, ctypes.byref(hw)))
+    return rp, col, (w if hw.value else None)
 
 
 def ad_graph_set_edge_weights(g, w_edge):

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <atomic>
@@ -132,6 +133,55 @@ template <> struct Store<__nv_bfloat16> {
     }
 };
 
+template <> struct Store<__half> {
+    static constexpr int V = 8;
+    __device__ __forceinline__ static void unpack2(uint32_t w, float &lo, float &hi) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+        lo = f.x;
+        hi = f.y;
+    }
+    __device__ __forceinline__ static void unpack(const uint4 &q, float *f) {
+        unpack2(q.x, f[0], f[1]); unpack2(q.y, f[2], f[3]);
+        unpack2(q.z, f[4], f[5]); unpack2(q.w, f[6], f[7]);
+    }
+    __device__ __forceinline__ static uint32_t pack2(float lo, float hi) {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+    __device__ __forceinline__ static uint4 pack(const float *f) {
+        return make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    }
+    __device__ __forceinline__ static float round(float f) { return __half2float(__float2half_rn(f)); }
+};
+
+// 16-bit fixed point: q in [-32768, 32767] stands for q * 2^-16 (covers [-1/2, 1/2)).
+struct Q16 {
+    int16_t q;
+};
+template <> struct Store<Q16> {
+    static constexpr int V = 8;
+    static constexpr float kStep = 1.52587890625e-5f;   // 2^-16
+    __device__ __forceinline__ static void unpack2(uint32_t w, float &lo, float &hi) {
+        lo = (float)((int32_t)(w << 16) >> 16) * kStep;
+        hi = (float)((int32_t)w >> 16) * kStep;
+    }
+    __device__ __forceinline__ static void unpack(const uint4 &q, float *f) {
+        unpack2(q.x, f[0], f[1]); unpack2(q.y, f[2], f[3]);
+        unpack2(q.z, f[4], f[5]); unpack2(q.w, f[6], f[7]);
+    }
+    __device__ __forceinline__ static int32_t code(float f) {
+        const int32_t c = __float2int_rn(f * 65536.0f);
+        return c < -32768 ? -32768 : (c > 32767 ? 32767 : c);
+    }
+    __device__ __forceinline__ static uint32_t pack2(float lo, float hi) {
+        return ((uint32_t)code(lo) & 0xffffu) | ((uint32_t)code(hi) << 16);
+    }
+    __device__ __forceinline__ static uint4 pack(const float *f) {
+        return make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    }
+    __device__ __forceinline__ static float round(float f) { return (float)code(f) * kStep; }
+};
+
 // ----------------------------------------------------------------------------
 // Device memory owned by a handle
 // ----------------------------------------------------------------------------
@@ -198,6 +248,8 @@ struct ad_graph_s {
     int64_t *upos = nullptr;     // first CSR position of row i with col > i
     int64_t *eoff = nullptr;     // edge id of that position; eoff[n] = m
     int64_t *mirror = nullptr;   // [nnz] position of the reverse entry (built lazily)
+    int32_t *erow = nullptr;     // [nnz] row of each entry (built lazily)
+    int64_t *eid = nullptr;      // [nnz] edge id of each entry (built lazily)
     int32_t *deg_class = nullptr;  // [n] index of the row's degree among distinct degrees (lazy)
     int32_t n_deg_classes = 0;
     std::vector<int64_t> distinct_degrees;  // host copy, ascending
@@ -254,13 +306,24 @@ ad_status exclusive_scan_i64(ad_graph_t g, const int64_t *in, int64_t *out, int6
 // graph setup (graph.cu)
 ad_status graph_setup(ad_graph_t g, int32_t flags);
 ad_status build_row_plan(ad_graph_t g, int groups, int small_max, bool upper_only, RowPlan &plan);
-ad_status ensure_mirror(ad_graph_t g);
+ad_status ensure_mirror(ad_graph_t g);   // also builds erow and eid
 ad_status ensure_degree_classes(ad_graph_t g);
 ad_status recompute_degrees(ad_graph_t g);
 
-// algebraic distance (sweep.cu)
+// algebraic distance (sweep.cu).  With keep: the stored vectors after sweep
+// t = 0, every, 2 every, ... are copied to keep->ckpt[t / every] (as many as
+// given) and the min/max slots of all sweeps to keep->mm_copy.
+struct KeepSpec {
+    int every = 1;
+    std::vector<void *> ckpt;
+    uint32_t *mm_copy = nullptr;
+};
 ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, uint64_t seed,
-                             uint32_t stream_id, ad_storage storage, int32_t flags, float *rho_dev);
+                             uint32_t stream_id, ad_storage storage, int32_t flags, float *rho_dev,
+                             const KeepSpec *keep = nullptr);
+ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, const void *x_in, void *x_out,
+                     const uint32_t *pmin, const uint32_t *pmax, uint32_t *mn, uint32_t *mx);
+ad_status get_row_plan(ad_graph_t g, int groups, bool upper, RowPlan **out);
 
 // selection (select.cu)
 ad_status select_whole_graph(ad_graph_t g, const float *score_dev, double fraction, ad_mode mode,
@@ -271,6 +334,16 @@ ad_status select_per_node_at(ad_graph_t g, const float *score_dev, double e, ad_
                              uint8_t *keep_dev, int64_t *n_kept);
 
 ad_status check_scores(ad_graph_t g, const float *score);
+
+// sorting and compaction (sort.cu)
+ad_status radix_sort_pairs(ad_graph_t g, uint64_t *keys, int64_t *vals, int64_t n, const std::vector<int> &shifts);
+ad_status compact_flags(ad_graph_t g, const uint8_t *flag, int64_t n, int64_t **idx_out, int64_t *count);
+
+// graph creation shared by the ABI and the multilevel code (api.cu)
+ad_status create_impl(int32_t G, const int64_t *voff, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                      const float *weight, int32_t flags, void *stream, ad_graph_t *out);
+ad_status create_like(ad_graph_t parent, int64_t n, const int64_t *rp_dev, const int32_t *col_dev, const float *w_dev,
+                      ad_graph_t *out);
 
 // reverse mode (grad.cu)
 ad_status algebraic_distance_keep(ad_graph_t g, int32_t R, int32_t k, double omega, uint64_t seed,

@@ -241,6 +241,11 @@ ad_status create_impl(int32_t G, const int64_t *voff, int64_t n, const int64_t *
     *out = g;
     return AD_OK;
 }
+ad_status create_like(ad_graph_t parent, int64_t n, const int64_t *rp_dev, const int32_t *col_dev, const float *w_dev,
+                      ad_graph_t *out) {
+    const int64_t voff[2] = {0, n};
+    return create_impl(1, voff, n, rp_dev, col_dev, w_dev, AD_CREATE_SKIP_VALIDATION, (void *)parent->stream, out);
+}
 }  // namespace ad
 
 extern "C" ad_status ad_graph_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const float *weight,
@@ -273,6 +278,17 @@ extern "C" ad_status ad_graph_info(ad_graph_t g, int64_t *n, int64_t *m, int64_t
     return AD_OK;
 }
 
+extern "C" ad_status ad_graph_export(ad_graph_t g, int64_t *row_ptr, int32_t *col, float *weight,
+                                     int32_t *has_weight) {
+    if (!g) return fail(AD_ERR_INVALID_ARG, "NULL graph");
+    if (row_ptr) AD_TRY(copy_out(g, row_ptr, g->rp, (g->n + 1) * sizeof(int64_t)));
+    if (col) AD_TRY(copy_out(g, col, g->col, g->nnz * sizeof(int32_t)));
+    if (weight && g->w) AD_TRY(copy_out(g, weight, g->w, g->nnz * sizeof(float)));
+    if (has_weight) *has_weight = g->w ? 1 : 0;
+    AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return AD_OK;
+}
+
 extern "C" ad_status ad_graph_edge_offsets(ad_graph_t g, int64_t *edge_offset) {
     if (!g || !edge_offset) return fail(AD_ERR_INVALID_ARG, "NULL argument");
     memcpy(edge_offset, g->eoff_h.data(), sizeof(int64_t) * (g->G + 1));
@@ -280,19 +296,14 @@ extern "C" ad_status ad_graph_edge_offsets(ad_graph_t g, int64_t *edge_offset) {
 }
 
 namespace ad {
-__global__ void k_scatter_edge_weights(const int64_t *rp, const int32_t *col, const int64_t *upos, const int64_t *eoff,
-                                       const int64_t *mirror, int64_t n, const float *we, float *w,
+__global__ void k_scatter_edge_weights(const int64_t *eid, int64_t nnz, const float *we, float *w,
                                        unsigned long long *bad) {
-    const int lane = threadIdx.x & 31;
-    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W)
-        for (int64_t p = upos[i] + lane; p < rp[i + 1]; p += 32) {
-            const int64_t e = eoff[i] + (p - upos[i]);
-            const float x = we[e];
-            if (!(x > 0.f) || !isfinite(x)) atomicMin(bad, (unsigned long long)e);
-            w[p] = x;
-            if (mirror[p] >= 0) w[mirror[p]] = x;
-        }
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = eid[p];
+        const float x = we[e];
+        if (!(x > 0.f) || !isfinite(x)) atomicMin(bad, (unsigned long long)e);
+        w[p] = x;
+    }
 }
 }  // namespace ad
 
@@ -306,9 +317,9 @@ extern "C" ad_status ad_graph_set_edge_weights(ad_graph_t g, const float *w_edge
     unsigned long long *bad = nullptr;
     AD_TRY(dalloc_t(g, 1, &bad));
     AD_CUDA_TRY(cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long), g->stream));
-    const int64_t blocks = std::min<int64_t>((g->n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
-    AD_LAUNCH(k_scatter_edge_weights, (int)blocks, 256, 0, g->stream, g->rp, g->col, g->upos, g->eoff, g->mirror, g->n,
-              (const float *)src, g->w, bad);
+    if (g->nnz > 0)
+        AD_LAUNCH(k_scatter_edge_weights, g->num_sms * 16, 256, 0, g->stream, g->eid, g->nnz, (const float *)src, g->w,
+                  bad);
     unsigned long long b = 0;
     AD_TRY(copy_out(g, &b, bad, sizeof(b)));
     dfree(g, bad);
@@ -328,7 +339,7 @@ extern "C" ad_status ad_algebraic_distance(ad_graph_t g, int32_t R, int32_t k, d
     if (R < 1 || R > 256) return fail(AD_ERR_INVALID_ARG, "R must be in [1, 256]");
     if (k < 0) return fail(AD_ERR_INVALID_ARG, "k must be >= 0");
     if (!(omega > 0.0 && omega <= 1.0)) return fail(AD_ERR_INVALID_ARG, "omega must be in (0, 1]");
-    if (storage != AD_STORAGE_FP32 && storage != AD_STORAGE_BF16) return fail(AD_ERR_INVALID_ARG, "bad storage");
+    if (storage < AD_STORAGE_FP32 || storage > AD_STORAGE_Q16) return fail(AD_ERR_INVALID_ARG, "bad storage");
     if (flags & ~(AD_DIST_NORMALIZE | AD_DIST_KEEP_STATE)) return fail(AD_ERR_INVALID_ARG, "unknown flags");
     if ((flags & AD_DIST_KEEP_STATE) && (storage != AD_STORAGE_FP32 || (flags & AD_DIST_NORMALIZE)))
         return fail(AD_ERR_INVALID_ARG, "kept state needs FP32 storage and no normalisation");

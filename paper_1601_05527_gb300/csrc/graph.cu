@@ -173,33 +173,61 @@ __global__ void k_degrees(const int64_t *rp, const int32_t *col, const float *w,
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W) {
         const int64_t b = rp[i], e = rp[i + 1];
-        double s = 0.0;
+        double s;
         if (w) {
-            for (int64_t p = b + lane; p < e; p += 32) s += (double)w[p];
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four independent loads in flight per lane
+            int64_t p = b + lane;
+            for (; p + 96 < e; p += 128) {
+                s0 += (double)w[p];
+                s1 += (double)w[p + 32];
+                s2 += (double)w[p + 64];
+                s3 += (double)w[p + 96];
+            }
+            for (; p < e; p += 32) s0 += (double)w[p];
+            s = (s0 + s1) + (s2 + s3);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         } else {
             s = (double)(e - b);
         }
-        // first position with col > i: count the entries with col < i
-        int64_t below = 0;
-        for (int64_t p = b + lane; p < e; p += 32) below += (col[p] < i) ? 1 : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
         if (lane == 0) {
+            // first position with col > i (rows are sorted)
+            int64_t lo = b, hi = e;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (col[mid] <= i) lo = mid + 1; else hi = mid;
+            }
             D[i] = s;
             Dinv[i] = s > 0.0 ? (float)(1.0 / s) : 0.f;
-            upos[i] = b + below;
-            ucount[i] = e - (b + below);
+            upos[i] = lo;
+            ucount[i] = e - lo;
         }
     }
 }
 
-__global__ void k_mirror(const int64_t *rp, const int32_t *col, int64_t n, int64_t *mirror) {
+// row of every entry (stores only, so a warp per row is cheap even for hubs)
+__global__ void k_entry_rows(const int64_t *rp, int64_t n, int32_t *erow) {
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W)
-        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) mirror[p] = find_in_row(rp, col, col[p], (int32_t)i);
+        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) erow[p] = (int32_t)i;
+}
+
+// one thread per entry: position of the reverse entry (binary search in row col[p])
+__global__ void k_mirror(const int64_t *rp, const int32_t *col, const int32_t *erow, int64_t nnz, int64_t *mirror) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        mirror[p] = find_in_row(rp, col, col[p], erow[p]);
+}
+
+// one thread per entry: the id of its edge (upper entries numbered row-major)
+__global__ void k_entry_eids(const int32_t *col, const int32_t *erow, const int64_t *upos, const int64_t *eoff,
+                             const int64_t *mirror, int64_t nnz, int64_t *eid) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = erow[p], j = col[p];
+        if (j > i) { eid[p] = eoff[i] + (p - upos[i]); continue; }
+        const int64_t q = mirror[p];   // -1 only for unvalidated asymmetric input
+        eid[p] = q >= 0 ? eoff[j] + (q - upos[j]) : eoff[i];
+    }
 }
 
 ad_status recompute_degrees(ad_graph_t g) {
@@ -273,9 +301,14 @@ ad_status graph_setup(ad_graph_t g, int32_t flags) {
 
 ad_status ensure_mirror(ad_graph_t g) {
     if (g->mirror || g->nnz == 0) return AD_OK;
+    AD_TRY(dalloc_t(g, g->nnz, &g->erow));
     AD_TRY(dalloc_t(g, g->nnz, &g->mirror));
-    const int64_t blocks = std::min<int64_t>((g->n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
-    AD_LAUNCH(k_mirror, (int)blocks, 256, 0, g->stream, g->rp, g->col, g->n, g->mirror);
+    AD_TRY(dalloc_t(g, g->nnz, &g->eid));
+    const int64_t wblocks = std::min<int64_t>((g->n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
+    AD_LAUNCH(k_entry_rows, (int)wblocks, 256, 0, g->stream, g->rp, g->n, g->erow);
+    const int grid = g->num_sms * 16;
+    AD_LAUNCH(k_mirror, grid, 256, 0, g->stream, g->rp, g->col, g->erow, g->nnz, g->mirror);
+    AD_LAUNCH(k_entry_eids, grid, 256, 0, g->stream, g->col, g->erow, g->upos, g->eoff, g->mirror, g->nnz, g->eid);
     return AD_OK;
 }
 

@@ -232,25 +232,23 @@ __global__ void k_sel_write(const float *score, int desc, const int32_t *tg, con
 // ----------------------------------------------------------------------------
 // Per-node ranks
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ int64_t edge_of_entry(const int64_t *rp, const int32_t *col, const int64_t *upos,
-                                                 const int64_t *eoff, const int64_t *mirror, int64_t i, int64_t p) {
-    const int32_t j = col[p];
-    if (j > i) return eoff[i] + (p - upos[i]);
-    const int64_t q = mirror[p];   // -1 only for unvalidated asymmetric input
-    return q >= 0 ? eoff[j] + (q - upos[j]) : eoff[i];
+__global__ void k_entry_keys(const int64_t *eid, int64_t nnz, const float *score, int desc, uint32_t *ekey) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        ekey[p] = score_key(score[eid[p]], desc);
 }
 
-__global__ void k_entry_keys(const int64_t *rp, const int32_t *col, const int64_t *upos, const int64_t *eoff,
-                             const int64_t *mirror, int64_t n, const float *score, int desc, uint32_t *ekey) {
-    const int lane = threadIdx.x & 31;
-    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W)
-        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32)
-            ekey[p] = score_key(score[edge_of_entry(rp, col, upos, eoff, mirror, i, p)], desc);
+// The rank r of entry p of row i goes to its edge's info: (rank at the lower
+// endpoint, rank at the upper endpoint, degree class of each endpoint).
+__device__ __forceinline__ void put_rank(int4 *info, const int64_t *eid, const int32_t *col, const int32_t *dc,
+                                         int64_t i, int64_t p, uint32_t r) {
+    int *f = reinterpret_cast<int *>(info + eid[p]);
+    if (col[p] > i) { f[0] = (int)r; f[2] = dc[i]; }
+    else { f[1] = (int)r; f[3] = dc[i]; }
 }
 
 // rows of degree <= 32: one warp each, rank by pairwise comparison
-__global__ void k_rank_small(const int64_t *rp, int64_t n, const uint32_t *ekey, uint32_t *rank) {
+__global__ void k_rank_small(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc, int64_t n,
+                             const uint32_t *ekey, int4 *info) {
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W) {
@@ -263,7 +261,24 @@ __global__ void k_rank_small(const int64_t *rp, int64_t n, const uint32_t *ekey,
             const uint32_t o = __shfl_sync(0xffffffffu, k, l);
             r += (o < k || (o == k && l < lane)) ? 1u : 0u;
         }
-        if (lane < d) rank[p0 + lane] = r;
+        if (lane < d) put_rank(info, eid, col, dc, i, p0 + lane, r);
+    }
+}
+
+// rows of degree in (32, kSortCap]: a CTA per row ranks by counting in shared memory
+__global__ void k_rank_mid(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
+                           const int32_t *rows, const uint32_t *ekey, int4 *info) {
+    __shared__ unsigned long long a[2048];
+    const int64_t row = rows[blockIdx.x];
+    const int64_t p0 = rp[row];
+    const int d = (int)(rp[row + 1] - p0);
+    for (int t = threadIdx.x; t < d; t += blockDim.x) a[t] = ((unsigned long long)ekey[p0 + t] << 32) | (unsigned)t;
+    __syncthreads();
+    for (int t = threadIdx.x; t < d; t += blockDim.x) {
+        const unsigned long long k = a[t];
+        uint32_t r = 0;
+        for (int u = 0; u < d; ++u) r += a[u] < k ? 1u : 0u;
+        put_rank(info, eid, col, dc, row, p0 + t, r);
     }
 }
 
@@ -285,7 +300,8 @@ __device__ void block_bitonic(unsigned long long *a, int len_pow2) {
     }
 }
 
-// rows of degree > 32: one CTA per (row, chunk of kSortCap entries)
+// rows of degree > kSortCap: one CTA per (row, chunk of kSortCap entries) sorts
+// the chunk; k_rank_merge then adds the ranks from the other chunks
 __global__ void k_rank_chunks(const int64_t *rp, const int32_t *rows, const int32_t *chunk, const uint32_t *ekey,
                               uint32_t *rank, unsigned long long *skey) {
     __shared__ unsigned long long a[kSortCap];
@@ -303,17 +319,17 @@ __global__ void k_rank_chunks(const int64_t *rp, const int32_t *rows, const int3
     for (int t = threadIdx.x; t < len; t += blockDim.x) {
         const int64_t pos = (int64_t)(a[t] & 0xffffffffull);
         rank[p0 + pos] = (uint32_t)t;
-        if (d > kSortCap) skey[p0 + c0 + t] = a[t];
+        skey[p0 + c0 + t] = a[t];
     }
 }
 
-// rows with several chunks: add the number of smaller keys in every other chunk
-__global__ void k_rank_merge(const int64_t *rp, const int32_t *rows, const int32_t *chunk, const uint32_t *ekey,
-                             const unsigned long long *skey, uint32_t *rank) {
+// rows of several chunks: add the number of smaller keys in every other chunk
+__global__ void k_rank_merge(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
+                             const int32_t *rows, const int32_t *chunk, const uint32_t *ekey,
+                             const unsigned long long *skey, const uint32_t *rank, int4 *info) {
     const int64_t row = rows[blockIdx.x];
     const int c = chunk[blockIdx.x];
     const int64_t p0 = rp[row], d = rp[row + 1] - p0;
-    if (d <= kSortCap) return;
     const int nch = (int)((d + kSortCap - 1) / kSortCap);
     const int64_t c0 = (int64_t)c * kSortCap;
     const int len = (int)std::min<int64_t>(kSortCap, d - c0);
@@ -330,16 +346,16 @@ __global__ void k_rank_merge(const int64_t *rp, const int32_t *rows, const int32
             }
             add += (uint32_t)lo;
         }
-        rank[p0 + c0 + t] += add;
+        put_rank(info, eid, col, dc, row, p0 + c0 + t, rank[p0 + c0 + t] + add);
     }
 }
 
-__global__ void k_chunk_count(const int64_t *rp, int64_t n, int64_t *nch, int8_t *cls) {
+// tasks per row: mid rows (32, kSortCap] one, big rows one per chunk
+__global__ void k_chunk_count(const int64_t *rp, int64_t n, int64_t *nmid, int64_t *nbig) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = rp[i + 1] - rp[i];
-        const bool big = d > 32;
-        nch[i] = big ? (d + kSortCap - 1) / kSortCap : 0;
-        cls[i] = big ? 0 : -1;
+        nmid[i] = (d > 32 && d <= kSortCap) ? 1 : 0;
+        nbig[i] = d > kSortCap ? (d + kSortCap - 1) / kSortCap : 0;
     }
 }
 __global__ void k_chunk_expand(const int64_t *nch, const int64_t *first, int64_t n, int32_t *rows, int32_t *chunk) {
@@ -347,19 +363,6 @@ __global__ void k_chunk_expand(const int64_t *nch, const int64_t *first, int64_t
         for (int64_t c = 0; c < nch[i]; ++c) {
             rows[first[i] + c] = (int32_t)i;
             chunk[first[i] + c] = (int32_t)c;
-        }
-}
-
-// per edge: (rank at its lower endpoint, rank at its upper endpoint, degree classes)
-__global__ void k_edge_info(const int64_t *rp, const int32_t *col, const int64_t *upos, const int64_t *eoff,
-                            const int64_t *mirror, const int32_t *dc, int64_t n, const uint32_t *rank, int4 *info) {
-    const int lane = threadIdx.x & 31;
-    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W)
-        for (int64_t p = upos[i] + lane; p < rp[i + 1]; p += 32) {
-            const int32_t j = col[p];
-            const int64_t q = mirror[p];
-            info[eoff[i] + (p - upos[i])] = make_int4((int)rank[p], q >= 0 ? (int)rank[q] : 0x7fffffff, dc[i], dc[j]);
         }
 }
 
@@ -468,7 +471,7 @@ ad_status select_whole_graph(ad_graph_t g, const float *score, double fraction, 
     return AD_OK;
 }
 
-// Ranks of every CSR entry and the per-edge info of Alg. 2.
+// Ranks of every CSR entry, gathered per edge: the info of Alg. 2.
 static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, int4 **info_out) {
     AD_TRY(ensure_mirror(g));
     AD_TRY(ensure_degree_classes(g));
@@ -476,44 +479,54 @@ static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, i
     const int64_t n = g->n, nnz = g->nnz;
     uint32_t *ekey = nullptr, *rank = nullptr;
     unsigned long long *skey = nullptr;
-    int64_t *nch = nullptr, *first = nullptr;
-    int8_t *cls = nullptr;
+    int64_t *nmid = nullptr, *nbig = nullptr, *fmid = nullptr, *fbig = nullptr;
+    int4 *info = nullptr;
+    AD_TRY(dalloc_t(g, g->m + 1, &info));
     AD_TRY(dalloc_t(g, nnz + 1, &ekey));
-    AD_TRY(dalloc_t(g, nnz + 1, &rank));
+    const int grid = g->num_sms * 16;
+    if (nnz > 0) AD_LAUNCH(k_entry_keys, grid, 256, 0, g->stream, g->eid, nnz, score, desc, ekey);
     const int64_t wblocks = std::min<int64_t>((n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
-    AD_LAUNCH(k_entry_keys, (int)wblocks, 256, 0, g->stream, g->rp, g->col, g->upos, g->eoff, g->mirror, n, score,
-              desc, ekey);
-    AD_LAUNCH(k_rank_small, (int)wblocks, 256, 0, g->stream, g->rp, n, ekey, rank);
-    // rows of degree > 32 -> (row, chunk) tasks
-    AD_TRY(dalloc_t(g, n + 1, &nch));
-    AD_TRY(dalloc_t(g, n + 1, &first));
-    AD_TRY(dalloc_t(g, n + 1, &cls));
-    AD_LAUNCH(k_chunk_count, g->num_sms * 8, 256, 0, g->stream, g->rp, n, nch, cls);
-    int64_t ntask = 0;
-    AD_TRY(exclusive_scan_i64(g, nch, first, n, &ntask));
-    if (ntask > 0) {
+    AD_LAUNCH(k_rank_small, (int)wblocks, 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, n, ekey, info);
+    AD_TRY(dalloc_t(g, n + 1, &nmid));
+    AD_TRY(dalloc_t(g, n + 1, &nbig));
+    AD_TRY(dalloc_t(g, n + 1, &fmid));
+    AD_TRY(dalloc_t(g, n + 1, &fbig));
+    AD_LAUNCH(k_chunk_count, g->num_sms * 8, 256, 0, g->stream, g->rp, n, nmid, nbig);
+    int64_t n_mid = 0, n_big = 0;
+    AD_TRY(exclusive_scan_i64(g, nmid, fmid, n, &n_mid));
+    AD_TRY(exclusive_scan_i64(g, nbig, fbig, n, &n_big));
+    if (n_mid > 0) {
         int32_t *rows = nullptr, *chunk = nullptr;
-        AD_TRY(dalloc_t(g, ntask, &rows));
-        AD_TRY(dalloc_t(g, ntask, &chunk));
+        AD_TRY(dalloc_t(g, n_mid, &rows));
+        AD_TRY(dalloc_t(g, n_mid, &chunk));
+        AD_LAUNCH(k_chunk_expand, g->num_sms * 8, 256, 0, g->stream, nmid, fmid, n, rows, chunk);
+        AD_LAUNCH(k_rank_mid, (int)n_mid, 128, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows, ekey, info);
+        AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
+        dfree(g, rows);
+        dfree(g, chunk);
+    }
+    if (n_big > 0) {
+        int32_t *rows = nullptr, *chunk = nullptr;
+        AD_TRY(dalloc_t(g, n_big, &rows));
+        AD_TRY(dalloc_t(g, n_big, &chunk));
         AD_TRY(dalloc_t(g, nnz + 1, &skey));
-        AD_LAUNCH(k_chunk_expand, g->num_sms * 8, 256, 0, g->stream, nch, first, n, rows, chunk);
-        AD_LAUNCH(k_rank_chunks, (int)ntask, 512, 0, g->stream, g->rp, rows, chunk, ekey, rank, skey);
-        AD_LAUNCH(k_rank_merge, (int)ntask, 256, 0, g->stream, g->rp, rows, chunk, ekey, skey, rank);
+        AD_TRY(dalloc_t(g, nnz + 1, &rank));
+        AD_LAUNCH(k_chunk_expand, g->num_sms * 8, 256, 0, g->stream, nbig, fbig, n, rows, chunk);
+        AD_LAUNCH(k_rank_chunks, (int)n_big, 512, 0, g->stream, g->rp, rows, chunk, ekey, rank, skey);
+        AD_LAUNCH(k_rank_merge, (int)n_big, 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows, chunk, ekey,
+                  skey, rank, info);
         AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
         dfree(g, rows);
         dfree(g, chunk);
         dfree(g, skey);
+        dfree(g, rank);
     }
-    int4 *info = nullptr;
-    AD_TRY(dalloc_t(g, g->m + 1, &info));
-    AD_LAUNCH(k_edge_info, (int)wblocks, 256, 0, g->stream, g->rp, g->col, g->upos, g->eoff, g->mirror, g->deg_class,
-              n, rank, info);
     AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
     dfree(g, ekey);
-    dfree(g, rank);
-    dfree(g, nch);
-    dfree(g, first);
-    dfree(g, cls);
+    dfree(g, nmid);
+    dfree(g, nbig);
+    dfree(g, fmid);
+    dfree(g, fbig);
     *info_out = info;
     return AD_OK;
 }

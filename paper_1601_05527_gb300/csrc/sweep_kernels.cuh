@@ -1,0 +1,619 @@
+// sweep_kernels.cuh -- kernels of ComputeAlgDist (Alg. 1) on sm_103a: Philox
+// init, JOR sweeps with the per-sweep rescale fused into the epilogue, and the
+// per-edge distance.  Instantiated once per storage type (sweep_<type>.cu).
+//
+// Data layout: the R test vectors of vertex i form row i of X[n][stride]
+// (stride = lanes_per_row * chunks_per_lane * V elements, 16-byte chunks,
+// V = 4 FP32 or 8 BF16 values).  A lane group of LPR lanes owns one row at a
+// time; lane gl of the group holds chunks gl, gl + LPR, ... of the row.
+//
+// Rescale.  Sweep t stores the raw update z = (1-omega) y_i + omega D_i^-1 sum_j
+// w_ij y_j applied to the stored values y of sweep t-1, mapped through the
+// affine x = a y + b that rescales sweep t-1 to [-1/2, 1/2]:
+//     sum_j w_ij (a y_j + b) = a sum_j w_ij y_j + b D_i,
+// so the stored value of sweep t is a z + b (the JOR operator commutes with
+// per-vector affine maps).  Each sweep reduces min/max of what it stores; the
+// next launch turns them into (a, b).  The distance of Alg. 1 uses the last
+// affine: rho = sqrt(sum_r a_r^2 (y_i^r - y_j^r)^2).
+#pragma once
+#include "ad_internal.cuh"
+
+#include <cmath>
+#include <cstring>
+
+namespace ad {
+
+struct SweepArgs {
+    const int64_t *rp;
+    const int32_t *col;
+    const float *w;        // nullable
+    const float *Dinv;
+    const double *D;
+    const int64_t *upos;   // distance: first upper entry
+    const int64_t *eoff;   // distance: edge id of that entry
+    const void *x_in;
+    void *x_out;
+    float *part;           // [n_big][stride] partial sums of big rows
+    const uint32_t *mm_prev_min, *mm_prev_max;  // nullptr at t = 0
+    uint32_t *mm_min, *mm_max;                  // this sweep's min/max
+    float *rho;            // distance output
+    // plan
+    const int32_t *big_row, *big_chunk, *medium_row, *small_row;
+    uint32_t *big_counter;
+    int64_t n_big, n_medium, n_small_rows;
+    int64_t n_tasks;
+    int32_t stride;        // elements per row
+    int32_t nchunks;       // valid 16-byte chunks per row (ceil(R / V))
+    int32_t R;
+    float omega;
+    int32_t normalize;
+    // batches: graph gph owns rows [voff[gph], voff[gph+1]); min/max slots are
+    // [G][stride] per sweep.  Batched launches give each warp a contiguous
+    // block of tasks so that consecutive rows mostly share one graph.
+    const int64_t *voff;
+    int32_t G;
+    int32_t blocked;
+};
+
+__device__ __forceinline__ int graph_of(const int64_t *voff, int G, int64_t row) {
+    int lo = 0, hi = G;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(voff + mid) <= row) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// task index range of warp `wid` among `W` warps: [t, t_end) stepping `step`
+struct TaskIter {
+    int64_t t, t_end, step;
+};
+__device__ __forceinline__ TaskIter task_iter(int64_t n_tasks, int64_t wid, int64_t W, int blocked) {
+    TaskIter it;
+    if (blocked) {
+        const int64_t per = (n_tasks + W - 1) / W;
+        it.t = wid * per;
+        it.t_end = min(n_tasks, it.t + per);
+        it.step = 1;
+    } else {
+        it.t = wid;
+        it.t_end = n_tasks;
+        it.step = W;
+    }
+    return it;
+}
+
+// ----------------------------------------------------------------------------
+// Init: x[i][r] = rand(-0.5, 0.5) from Philox, counter (i, r/4, stream), i the
+// vertex id inside its graph.  One thread per (row, quad of vectors); rows of
+// degree 0 are skipped.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void k_init(const int64_t *__restrict__ rp, int64_t n, int32_t stride, uint32_t seed_lo,
+                       uint32_t seed_hi, uint32_t stream_id, const int64_t *voff, int G, T *__restrict__ x) {
+    const int32_t quads = stride / 4;
+    const int64_t total = n * quads;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / quads;
+        const int32_t q = (int32_t)(t - i * quads);
+        if (rp[i + 1] == rp[i]) continue;
+        const int64_t li = G > 1 ? i - voff[graph_of(voff, G, i)] : i;   // id inside its graph
+        uint4 c = make_uint4((uint32_t)((uint64_t)li), (uint32_t)((uint64_t)li >> 32), (uint32_t)q, stream_id);
+        uint4 u = philox4x32_10(c, make_uint2(seed_lo, seed_hi));
+        float v[4] = {unit_centered(u.x), unit_centered(u.y), unit_centered(u.z), unit_centered(u.w)};
+        T *dst = x + i * stride + 4 * q;
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            uint2 p = make_uint2(Store<T>::pack2(v[0], v[1]), Store<T>::pack2(v[2], v[3]));
+            *reinterpret_cast<uint2 *>(dst) = p;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Helpers for the lane-group kernels
+// ----------------------------------------------------------------------------
+template <typename T, int LPR, int CPL>
+struct Lane {
+    static constexpr int V = Store<T>::V;
+    static constexpr int E = CPL * V;       // elements held by one lane
+    static constexpr int G = 32 / LPR;      // groups per warp
+};
+
+// Gather-accumulate rows col[p] for p in [p0, p1) with the whole warp: group
+// grp takes every G-th neighbour.  Column indices (and weights) are read 32 at
+// a time, coalesced, and broadcast with shuffles; each lane then issues up to
+// UB independent 16-byte row loads before it consumes any of them, so that
+// enough requests are in flight to cover the L2 latency.
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int64_t p1, int lane, int grp,
+                                            int gl, float (&acc)[CPL * Store<T>::V]) {
+    using L = Lane<T, LPR, CPL>;
+    constexpr int V = L::V, G = L::G;
+    constexpr int U = 32 / G;                       // neighbours per group per batch of 32
+    constexpr int UB = (8 / CPL) < U ? (8 / CPL) : U;   // loads in flight per chunk slot
+    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
+    const int64_t row_q = a.stride / V;   // 16-byte chunks per row
+    for (int64_t base = p0; base < p1; base += 32) {
+        const int64_t p = base + lane;
+        int32_t cj = 0;
+        float wj = 0.f;
+        if (p < p1) {
+            cj = __ldg(a.col + p);
+            wj = a.w ? __ldg(a.w + p) : 1.f;
+        }
+        const int cnt = (int)(p1 - base < 32 ? p1 - base : 32);
+#pragma unroll
+        for (int u0 = 0; u0 < U; u0 += UB) {
+            if (u0 * G >= cnt) break;
+            uint4 v[UB][CPL];
+            float wt[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int src = (u0 + u) * G + grp;
+                const int32_t nb = __shfl_sync(0xffffffffu, cj, src);
+                wt[u] = __shfl_sync(0xffffffffu, wj, src);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const int q = gl + c * LPR;
+                    v[u][c] = (src < cnt && q < a.nchunks) ? __ldg(X + (int64_t)nb * row_q + q) : make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u)
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    float f[V];
+                    Store<T>::unpack(v[u][c], f);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) acc[c * V + e] = fmaf(wt[u], f[e], acc[c * V + e]);
+                }
+        }
+    }
+}
+
+// Gather-accumulate a short row (<= kSmallUnroll entries per round) with one
+// lane group: all of its column indices, then all row loads, then the sums.
+constexpr int kSmallUnroll = 8;
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void group_gather(const SweepArgs &a, int64_t p0, int64_t p1, int gl,
+                                             float (&acc)[CPL * Store<T>::V]) {
+    constexpr int V = Store<T>::V;
+    constexpr int UB = (kSmallUnroll / CPL) > 0 ? (kSmallUnroll / CPL) : 1;
+    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
+    const int64_t row_q = a.stride / V;
+    for (int64_t base = p0; base < p1; base += UB) {
+        int32_t nb[UB];
+        float wt[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const bool ok = base + u < p1;
+            nb[u] = ok ? __ldg(a.col + base + u) : 0;
+            wt[u] = ok ? (a.w ? __ldg(a.w + base + u) : 1.f) : 0.f;
+        }
+        uint4 v[UB][CPL];
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                const int q = gl + c * LPR;
+                v[u][c] = (base + u < p1 && q < a.nchunks) ? __ldg(X + (int64_t)nb[u] * row_q + q) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                float f[V];
+                Store<T>::unpack(v[u][c], f);
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[c * V + e] = fmaf(wt[u], f[e], acc[c * V + e]);
+            }
+    }
+}
+
+// Sum over the G groups of a warp (butterfly: every group ends with the total).
+template <int LPR, int E>
+__device__ __forceinline__ void reduce_groups(float (&acc)[E]) {
+#pragma unroll
+    for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], off);
+}
+
+// Epilogue of a row: z = (1-omega) y_i + omega Dinv_i S, store a z + b, track min/max.
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, int gl,
+                                             const float (&S)[CPL * Store<T>::V],
+                                             const float (&A)[CPL * Store<T>::V],
+                                             const float (&B)[CPL * Store<T>::V],
+                                             float (&mn)[CPL * Store<T>::V], float (&mx)[CPL * Store<T>::V]) {
+    constexpr int V = Store<T>::V;
+    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
+    uint4 *Y = reinterpret_cast<uint4 *>(a.x_out);
+    const int64_t row_q = a.stride / V;
+    const float dinv = __ldg(a.Dinv + row);
+    const float om = a.omega, om1 = 1.f - a.omega;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        const int q = gl + c * LPR;
+        if (q < a.nchunks) {
+            float y[V], o[V];
+            Store<T>::unpack(__ldg(X + row * row_q + q), y);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const float z = fmaf(om1, y[e], om * (S[c * V + e] * dinv));
+                o[e] = Store<T>::round(fmaf(A[c * V + e], z, B[c * V + e]));
+                mn[c * V + e] = fminf(mn[c * V + e], o[e]);
+                mx[c * V + e] = fmaxf(mx[c * V + e], o[e]);
+            }
+            Y[row * row_q + q] = Store<T>::pack(o);
+        }
+    }
+}
+
+// Affine (a, b) of the previous sweep's rescale for the lane's elements.
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void load_affine(const uint32_t *pmin, const uint32_t *pmax, int gl,
+                                            float (&A)[CPL * Store<T>::V], float (&B)[CPL * Store<T>::V]) {
+    // pmin / pmax point at the slots of the row's graph (nullptr: no rescale yet)
+    constexpr int V = Store<T>::V;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c)
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const int r = (gl + c * LPR) * V + e;
+            float av = 1.f, bv = 0.f;
+            if (pmin) {
+                const double lo = ord2f(pmin[r]), hi = ord2f(pmax[r]);
+                if (hi > lo) {
+                    const double s = 1.0 / (hi - lo);
+                    av = (float)s;
+                    bv = (float)(-lo * s - 0.5);
+                } else {
+                    av = 0.f;
+                    bv = 0.f;
+                }
+            }
+            A[c * V + e] = av;
+            B[c * V + e] = bv;
+        }
+}
+
+// ----------------------------------------------------------------------------
+// Running min/max of the values a lane stores, for the graph `cg` of the rows
+// it handled last; flushed with atomics when the lane moves to another graph.
+// ----------------------------------------------------------------------------
+template <typename T, int LPR, int CPL>
+struct LaneStats {
+    static constexpr int V = Store<T>::V, E = CPL * V;
+    float A[E], B[E], mn[E], mx[E];
+    int cg = -1;
+
+    __device__ __forceinline__ void flush(const SweepArgs &a, int gl) {
+        if (cg < 0) return;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const int r = (gl + c * LPR) * V + e;
+                if ((gl + c * LPR) < a.nchunks && mn[c * V + e] <= mx[c * V + e]) {
+                    atomicMin(a.mm_min + (size_t)cg * a.stride + r, f2ord(mn[c * V + e]));
+                    atomicMax(a.mm_max + (size_t)cg * a.stride + r, f2ord(mx[c * V + e]));
+                }
+            }
+    }
+    // make the lane's state describe graph `g` (affine of its previous sweep)
+    __device__ __forceinline__ void enter(const SweepArgs &a, int gl, int g, bool flush_old) {
+        if (g == cg) return;
+        if (flush_old) flush(a, gl);
+        cg = g;
+        load_affine<T, LPR, CPL>(a.mm_prev_min ? a.mm_prev_min + (size_t)g * a.stride : nullptr,
+                                 a.mm_prev_max ? a.mm_prev_max + (size_t)g * a.stride : nullptr, gl, A, B);
+#pragma unroll
+        for (int e = 0; e < E; ++e) { mn[e] = INFINITY; mx[e] = -INFINITY; }
+    }
+};
+
+// ----------------------------------------------------------------------------
+// One JOR sweep (Alg. 1 inner loop) over all rows of degree > 0.
+// ----------------------------------------------------------------------------
+template <typename T, int LPR, int CPL>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
+    using L = Lane<T, LPR, CPL>;
+    constexpr int V = L::V, E = L::E, G = L::G;
+    extern __shared__ float sm[];   // [2][warps][stride]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int grp = lane / LPR, gl = lane % LPR;
+
+    LaneStats<T, LPR, CPL> ls;
+    ls.enter(a, gl, 0, false);
+    auto row_graph = [&](int64_t row) { return a.G > 1 ? graph_of(a.voff, a.G, row) : 0; };
+
+    const int64_t W = (int64_t)gridDim.x * nwarps;
+    const TaskIter it = task_iter(a.n_tasks, (int64_t)blockIdx.x * nwarps + warp, W, a.blocked);
+    for (int64_t task = it.t; task < it.t_end; task += it.step) {
+        float acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        if (task < a.n_big) {
+            // ---- a chunk of a high-degree row; the last chunk combines
+            const int64_t row = a.big_row[task];
+            const int32_t c = a.big_chunk[task];
+            const int64_t rb = a.rp[row], re = a.rp[row + 1];
+            const int64_t p0 = rb + (int64_t)c * kChunk, p1 = min(re, p0 + kChunk);
+            warp_gather<T, LPR, CPL>(a, p0, p1, lane, grp, gl, acc);
+            reduce_groups<LPR, E>(acc);
+            float *part = a.part + task * (int64_t)a.stride;
+            if (grp == 0) {
+#pragma unroll
+                for (int cc = 0; cc < CPL; ++cc) {
+                    const int q = gl + cc * LPR;
+                    if (q < a.nchunks) {
+#pragma unroll
+                        for (int e = 0; e < V; ++e) __stcg(part + q * V + e, acc[cc * V + e]);
+                    }
+                }
+                __threadfence();
+            }
+            __syncwarp();
+            const int64_t t0 = task - c;
+            const int32_t nchunk = (int32_t)((re - rb + kChunk - 1) / kChunk);
+            uint32_t old = 0;
+            if (lane == 0) old = atomicAdd(a.big_counter + t0, 1u);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old == (uint32_t)(nchunk - 1)) {
+                __threadfence();
+                if (grp == 0) {
+                    float S[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) S[e] = 0.f;
+                    for (int32_t cc2 = 0; cc2 < nchunk; ++cc2) {
+                        const float *pp = a.part + (t0 + cc2) * (int64_t)a.stride;
+#pragma unroll
+                        for (int cc = 0; cc < CPL; ++cc) {
+                            const int q = gl + cc * LPR;
+                            if (q < a.nchunks) {
+#pragma unroll
+                                for (int e = 0; e < V; ++e) S[cc * V + e] += __ldcg(pp + q * V + e);
+                            }
+                        }
+                    }
+                    ls.enter(a, gl, row_graph(row), true);
+                    row_epilogue<T, LPR, CPL>(a, row, gl, S, ls.A, ls.B, ls.mn, ls.mx);
+                }
+                if (lane == 0) a.big_counter[t0] = 0u;
+            }
+        } else if (task < a.n_big + a.n_medium) {
+            // ---- one row, whole warp
+            const int64_t row = a.medium_row[task - a.n_big];
+            warp_gather<T, LPR, CPL>(a, a.rp[row], a.rp[row + 1], lane, grp, gl, acc);
+            reduce_groups<LPR, E>(acc);
+            if (grp == 0) {
+                ls.enter(a, gl, row_graph(row), true);
+                row_epilogue<T, LPR, CPL>(a, row, gl, acc, ls.A, ls.B, ls.mn, ls.mx);
+            }
+        } else {
+            // ---- G low-degree rows, one per lane group
+            const int64_t si = (task - a.n_big - a.n_medium) * G + grp;
+            if (si < a.n_small_rows) {
+                const int64_t row = a.small_row[si];
+                group_gather<T, LPR, CPL>(a, a.rp[row], a.rp[row + 1], gl, acc);
+                ls.enter(a, gl, row_graph(row), true);
+                row_epilogue<T, LPR, CPL>(a, row, gl, acc, ls.A, ls.B, ls.mn, ls.mx);
+            }
+        }
+    }
+
+    // ---- min/max of what this CTA stored -> atomics
+    if (a.G > 1) {
+        // lanes of a warp that share one graph are reduced first
+        const bool same = __all_sync(0xffffffffu, ls.cg == __shfl_sync(0xffffffffu, ls.cg, 0));
+        if (same) {
+#pragma unroll
+            for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    ls.mn[e] = fminf(ls.mn[e], __shfl_xor_sync(0xffffffffu, ls.mn[e], off));
+                    ls.mx[e] = fmaxf(ls.mx[e], __shfl_xor_sync(0xffffffffu, ls.mx[e], off));
+                }
+            if (grp == 0) ls.flush(a, gl);
+        } else {
+            ls.flush(a, gl);
+        }
+        return;
+    }
+#pragma unroll
+    for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            ls.mn[e] = fminf(ls.mn[e], __shfl_xor_sync(0xffffffffu, ls.mn[e], off));
+            ls.mx[e] = fmaxf(ls.mx[e], __shfl_xor_sync(0xffffffffu, ls.mx[e], off));
+        }
+    float *smn = sm, *smx = sm + nwarps * a.stride;
+    if (grp == 0) {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const int r = (gl + c * LPR) * V + e;
+                smn[warp * a.stride + r] = ls.mn[c * V + e];
+                smx[warp * a.stride + r] = ls.mx[c * V + e];
+            }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < a.nchunks * V; r += blockDim.x) {
+        float lo = INFINITY, hi = -INFINITY;
+        for (int wi = 0; wi < nwarps; ++wi) {
+            lo = fminf(lo, smn[wi * a.stride + r]);
+            hi = fmaxf(hi, smx[wi * a.stride + r]);
+        }
+        if (lo <= hi) {
+            atomicMin(a.mm_min + r, f2ord(lo));
+            atomicMax(a.mm_max + r, f2ord(hi));
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Edge distance: for every upper entry (i, j > i) of the CSR, edge id e =
+// eoff[i] + (p - upos[i]), rho_e = sqrt(sum_r a_r^2 (y_i^r - y_j^r)^2).
+// A lane group handles one edge; its lanes hold different chunks of R.
+// ----------------------------------------------------------------------------
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64_t p0, int64_t p1, int step,
+                                          int first, int gl, unsigned gmask, const float (&A2)[CPL * Store<T>::V]) {
+    constexpr int V = Store<T>::V, E = CPL * V;
+    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
+    const int64_t row_q = a.stride / V;
+    float yi[E];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        const int q = gl + c * LPR;
+        if (q < a.nchunks) Store<T>::unpack(__ldg(X + row * row_q + q), yi + c * V);
+        else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) yi[c * V + e] = 0.f;
+        }
+    }
+    const int64_t ebase = a.eoff[row] - a.upos[row];
+    const double Di = a.normalize ? a.D[row] : 0.0;
+    // the lanes of one group share p, so the group-masked reduction below is uniform
+    for (int64_t p = p0 + first; p < p1; p += step) {
+        const int32_t j = __ldg(a.col + p);
+        float s = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int q = gl + c * LPR;
+            if (q < a.nchunks) {
+                float yj[V];
+                Store<T>::unpack(__ldg(X + (int64_t)j * row_q + q), yj);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const float d = yi[c * V + e] - yj[e];
+                    s = fmaf(A2[c * V + e] * d, d, s);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
+        if (gl == 0) {
+            float rho = sqrtf(s);
+            if (a.normalize) rho = (float)((double)rho * sqrt(Di * a.D[j]));
+            a.rho[ebase + p] = rho;
+        }
+    }
+}
+
+template <typename T, int LPR, int CPL>
+__global__ void __launch_bounds__(256) k_distance(SweepArgs a) {
+    using L = Lane<T, LPR, CPL>;
+    constexpr int V = L::V, E = L::E, G = L::G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int grp = lane / LPR, gl = lane % LPR;
+    const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (grp * LPR));
+    float A[E], B[E], A2[E];
+    int cg = -1;
+    // squared scale of the last rescale of graph g; padded vectors r >= R excluded
+    auto enter = [&](int g) {
+        if (g == cg) return;
+        cg = g;
+        load_affine<T, LPR, CPL>(a.mm_prev_min ? a.mm_prev_min + (size_t)g * a.stride : nullptr,
+                                 a.mm_prev_max ? a.mm_prev_max + (size_t)g * a.stride : nullptr, gl, A, B);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const int r = (gl + c * LPR) * V + e;
+                A2[c * V + e] = (r < a.R) ? A[c * V + e] * A[c * V + e] : 0.f;
+            }
+    };
+    auto row_graph = [&](int64_t row) { return a.G > 1 ? graph_of(a.voff, a.G, row) : 0; };
+    const int64_t W = (int64_t)gridDim.x * nwarps;
+    const TaskIter it = task_iter(a.n_tasks, (int64_t)blockIdx.x * nwarps + warp, W, a.blocked);
+    for (int64_t task = it.t; task < it.t_end; task += it.step) {
+        if (task < a.n_big) {
+            const int64_t row = a.big_row[task];
+            const int32_t c = a.big_chunk[task];
+            const int64_t ub = a.upos[row], ue = a.rp[row + 1];
+            const int64_t p0 = ub + (int64_t)c * kChunk, p1 = min(ue, p0 + kChunk);
+            enter(row_graph(row));
+            edge_rows<T, LPR, CPL>(a, row, p0, p1, G, grp, gl, gmask, A2);
+        } else if (task < a.n_big + a.n_medium) {
+            const int64_t row = a.medium_row[task - a.n_big];
+            enter(row_graph(row));
+            edge_rows<T, LPR, CPL>(a, row, a.upos[row], a.rp[row + 1], G, grp, gl, gmask, A2);
+        } else {
+            const int64_t si = (task - a.n_big - a.n_medium) * G + grp;
+            if (si < a.n_small_rows) {
+                const int64_t row = a.small_row[si];
+                enter(row_graph(row));
+                edge_rows<T, LPR, CPL>(a, row, a.upos[row], a.rp[row + 1], 1, 0, gl, gmask, A2);
+            }
+        }
+    }
+}
+
+struct Config {
+    int lpr, cpl, V, stride, nchunks;
+};
+
+
+template <typename T, int LPR, int CPL>
+ad_status launch_sweep(ad_graph_t g, const SweepArgs &a, int blocks, size_t smem) {
+    AD_LAUNCH((k_sweep<T, LPR, CPL>), blocks, 256, smem, g->stream, a);
+    return AD_OK;
+}
+template <typename T, int LPR, int CPL>
+ad_status launch_distance(ad_graph_t g, const SweepArgs &a, int blocks) {
+    AD_LAUNCH((k_distance<T, LPR, CPL>), blocks, 256, 0, g->stream, a);
+    return AD_OK;
+}
+
+template <typename T, int LPR, int CPL>
+int blocks_for(bool sweep, size_t smem) {
+    int per_sm = 0;
+    if (sweep)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T, LPR, CPL>, 256, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_distance<T, LPR, CPL>, 256, 0);
+    return per_sm > 0 ? per_sm : 1;
+}
+
+template <typename T>
+ad_status dispatch(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &a, int64_t n_tasks,
+                          size_t smem) {
+    // persistent grid: every SM full, but no more warps than tasks
+    auto run = [&](auto lpr_c, auto cpl_c) -> ad_status {
+        constexpr int LPR = decltype(lpr_c)::value, CPL = decltype(cpl_c)::value;
+        int per_sm = blocks_for<T, LPR, CPL>(sweep, smem);
+        int64_t blocks = (int64_t)per_sm * g->num_sms;
+        const int64_t need = (n_tasks + 7) / 8;
+        if (blocks > need) blocks = need > 0 ? need : 1;
+        return sweep ? launch_sweep<T, LPR, CPL>(g, a, (int)blocks, smem)
+                     : launch_distance<T, LPR, CPL>(g, a, (int)blocks);
+    };
+    using std::integral_constant;
+    switch (cf.lpr * 100 + cf.cpl) {
+        case 101: return run(integral_constant<int, 1>{}, integral_constant<int, 1>{});
+        case 201: return run(integral_constant<int, 2>{}, integral_constant<int, 1>{});
+        case 401: return run(integral_constant<int, 4>{}, integral_constant<int, 1>{});
+        case 801: return run(integral_constant<int, 8>{}, integral_constant<int, 1>{});
+        case 1601: return run(integral_constant<int, 16>{}, integral_constant<int, 1>{});
+        case 3201: return run(integral_constant<int, 32>{}, integral_constant<int, 1>{});
+        case 3202: return run(integral_constant<int, 32>{}, integral_constant<int, 2>{});
+        default: return fail(AD_ERR_INVALID_ARG, "unsupported R / storage combination");
+    }
+}
+
+
+// one instantiation per storage type, each in its own translation unit
+ad_status dispatch_f32(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &a, int64_t n_tasks, size_t smem);
+ad_status dispatch_bf16(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &a, int64_t n_tasks, size_t smem);
+ad_status dispatch_f16(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &a, int64_t n_tasks, size_t smem);
+ad_status dispatch_q16(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &a, int64_t n_tasks, size_t smem);
+ad_status launch_init(ad_graph_t g, ad_storage storage, int blocks, int32_t stride, uint64_t seed, uint32_t stream_id,
+                      void *x);
+
+}  // namespace ad
