@@ -13,7 +13,7 @@ with host buffers (graph upload and result download inside the timed region),
 the HBM roofline fraction of the dominant kernel (one JOR sweep), and the FP64
 oracle timed on the host cores on a bounded sample of the same workload.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|bf16]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|bf16|fp16|q16]
     python bench.py --impl reference      # the FP64 CPU oracle, same metric
 """
 from __future__ import annotations
@@ -43,8 +43,10 @@ WORKLOAD = (f"R-MAT scale {SCALE} (2^{SCALE} vertices, edge factor {EDGE_FACTOR}
 
 
 def sweep_source_digest() -> str:
-    p = os.path.join(ROOT, "paper_1601_05527_gb300", "csrc", "sweep.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("sweep_kernels.cuh", "ad_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1601_05527_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -131,7 +133,7 @@ def algorithmic_bytes_per_sweep(g, storage):
     """Compulsory traffic of one sweep (gathers assumed served on chip): column
     indices, row pointers, inverse degrees, and one read + one write of every
     active row of the R-wide vector block."""
-    s = 2 if storage == "bf16" else 4
+    s = 4 if storage == "fp32" else 2
     n_active = int((g.degrees() > 0).sum())
     return g.nnz * 4 + (g.n + 1) * 4 + g.n * 4 + 2 * n_active * R * s, n_active
 
@@ -309,7 +311,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16", "q16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":

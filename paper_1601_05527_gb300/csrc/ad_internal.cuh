@@ -154,13 +154,14 @@ template <> struct Store<__half> {
     __device__ __forceinline__ static float round(float f) { return __half2float(__float2half_rn(f)); }
 };
 
-// 16-bit fixed point: q in [-32768, 32767] stands for q * 2^-16 (covers [-1/2, 1/2)).
+// 16-bit fixed point: q in [-32768, 32767] stands for q * 2^-15 (covers [-1, 1);
+// every stored value of a sweep lies in [-1, 1]).
 struct Q16 {
     int16_t q;
 };
 template <> struct Store<Q16> {
     static constexpr int V = 8;
-    static constexpr float kStep = 1.52587890625e-5f;   // 2^-16
+    static constexpr float kStep = 3.0517578125e-5f;   // 2^-15
     __device__ __forceinline__ static void unpack2(uint32_t w, float &lo, float &hi) {
         lo = (float)((int32_t)(w << 16) >> 16) * kStep;
         hi = (float)((int32_t)w >> 16) * kStep;
@@ -170,7 +171,7 @@ template <> struct Store<Q16> {
         unpack2(q.z, f[4], f[5]); unpack2(q.w, f[6], f[7]);
     }
     __device__ __forceinline__ static int32_t code(float f) {
-        const int32_t c = __float2int_rn(f * 65536.0f);
+        const int32_t c = __float2int_rn(f * 32768.0f);
         return c < -32768 ? -32768 : (c > 32767 ? 32767 : c);
     }
     __device__ __forceinline__ static uint32_t pack2(float lo, float hi) {
@@ -208,8 +209,11 @@ struct DevBuf {
 // Big tasks come first, then medium rows by decreasing degree class, then
 // small rows, so that warps striding over the task list meet similar work.
 // ----------------------------------------------------------------------------
-constexpr int kChunk = 512;
-constexpr int kBig = 512;
+#ifndef AD_CHUNK
+#define AD_CHUNK 512
+#endif
+constexpr int kChunk = AD_CHUNK;
+constexpr int kBig = AD_CHUNK;
 
 struct RowPlan {
     int small_max = 0;          // degree bound of the small class
@@ -257,6 +261,7 @@ struct ad_graph_s {
     // batches
     std::vector<int64_t> voff_h, eoff_h;   // vertex / edge offsets per graph (host)
     int64_t *voff = nullptr;               // device copies
+    int32_t *anchor = nullptr;             // [G] vertex of largest weighted degree of each graph
     int64_t *goff_e = nullptr;
 
     // work plans keyed by lane-group count

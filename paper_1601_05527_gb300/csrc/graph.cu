@@ -5,6 +5,7 @@
 #include "ad_internal.cuh"
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 
 namespace ad {
@@ -230,6 +231,43 @@ __global__ void k_entry_eids(const int32_t *col, const int32_t *erow, const int6
     }
 }
 
+// anchor of each graph: the vertex of largest weighted degree, ties to the smaller id
+__global__ void k_anchor_max(const double *D, const int64_t *voff, int G, int64_t n, unsigned long long *best) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int g = 0;
+        if (G > 1) { int lo = 0, hi = G; while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (voff[mid] <= i) lo = mid; else hi = mid; } g = lo; }
+        atomicMax(best + g, (unsigned long long)__double_as_longlong(D[i]));   // D >= 0: bits order like values
+    }
+}
+__global__ void k_anchor_pick(const double *D, const int64_t *voff, int G, int64_t n, const unsigned long long *best,
+                              int32_t *anchor) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int g = 0;
+        if (G > 1) { int lo = 0, hi = G; while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (voff[mid] <= i) lo = mid; else hi = mid; } g = lo; }
+        if ((unsigned long long)__double_as_longlong(D[i]) == best[g]) atomicMin(anchor + g, (int32_t)i);
+    }
+}
+
+static ad_status compute_anchors(ad_graph_t g) {
+    if (!g->anchor) AD_TRY(dalloc_t(g, g->G + 1, &g->anchor));
+    // non-empty graphs start at INT32_MAX and take the smallest id of maximum D;
+    // an empty graph keeps its first id (no kernel reads it)
+    std::vector<int32_t> init(g->G + 1, 0);
+    for (int32_t k = 0; k < g->G; ++k)
+        init[k] = g->voff_h[k + 1] > g->voff_h[k] ? INT32_MAX : (int32_t)std::min<int64_t>(g->voff_h[k], INT32_MAX);
+    AD_TRY(copy_in(g, g->anchor, init.data(), (g->G + 1) * sizeof(int32_t)));
+    if (g->n > 0) {
+        unsigned long long *best = nullptr;
+        AD_TRY(dalloc_t(g, g->G + 1, &best));
+        AD_CUDA_TRY(cudaMemsetAsync(best, 0, (g->G + 1) * sizeof(unsigned long long), g->stream));
+        AD_LAUNCH(k_anchor_max, g->num_sms * 8, 256, 0, g->stream, g->D, g->voff, g->G, g->n, best);
+        AD_LAUNCH(k_anchor_pick, g->num_sms * 8, 256, 0, g->stream, g->D, g->voff, g->G, g->n, best, g->anchor);
+        AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
+        dfree(g, best);
+    }
+    return AD_OK;
+}
+
 ad_status recompute_degrees(ad_graph_t g) {
     int64_t *ucount = nullptr;
     AD_TRY(dalloc_t(g, g->n + 1, &ucount));
@@ -243,7 +281,7 @@ ad_status recompute_degrees(ad_graph_t g) {
     AD_CUDA_TRY(cudaMemcpyAsync(g->eoff + g->n, &m, sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
     AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
     g->m = m;
-    return AD_OK;
+    return compute_anchors(g);
 }
 
 __global__ void k_count_active(const int64_t *rp, int64_t n, unsigned long long *cnt) {

@@ -265,23 +265,6 @@ __global__ void k_rank_small(const int64_t *rp, const int32_t *col, const int64_
     }
 }
 
-// rows of degree in (32, kSortCap]: a CTA per row ranks by counting in shared memory
-__global__ void k_rank_mid(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
-                           const int32_t *rows, const uint32_t *ekey, int4 *info) {
-    __shared__ unsigned long long a[2048];
-    const int64_t row = rows[blockIdx.x];
-    const int64_t p0 = rp[row];
-    const int d = (int)(rp[row + 1] - p0);
-    for (int t = threadIdx.x; t < d; t += blockDim.x) a[t] = ((unsigned long long)ekey[p0 + t] << 32) | (unsigned)t;
-    __syncthreads();
-    for (int t = threadIdx.x; t < d; t += blockDim.x) {
-        const unsigned long long k = a[t];
-        uint32_t r = 0;
-        for (int u = 0; u < d; ++u) r += a[u] < k ? 1u : 0u;
-        put_rank(info, eid, col, dc, row, p0 + t, r);
-    }
-}
-
 constexpr int kSortCap = 2048;   // entries sorted by one CTA in shared memory
 
 // Bitonic sort of up to kSortCap 64-bit keys (key << 32 | position) in smem.
@@ -298,6 +281,35 @@ __device__ void block_bitonic(unsigned long long *a, int len_pow2) {
             __syncthreads();
         }
     }
+}
+
+// rows of degree in (32, kSortCap]: a CTA per row; up to 128 entries rank by
+// counting, longer rows by a bitonic sort of (key, position) in shared memory
+__global__ void k_rank_mid(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
+                           const int32_t *rows, const uint32_t *ekey, int4 *info) {
+    __shared__ unsigned long long a[kSortCap];
+    const int64_t row = rows[blockIdx.x];
+    const int64_t p0 = rp[row];
+    const int d = (int)(rp[row + 1] - p0);
+    if (d <= 128) {
+        for (int t = threadIdx.x; t < d; t += blockDim.x) a[t] = ((unsigned long long)ekey[p0 + t] << 32) | (unsigned)t;
+        __syncthreads();
+        for (int t = threadIdx.x; t < d; t += blockDim.x) {
+            const unsigned long long k = a[t];
+            uint32_t r = 0;
+            for (int u = 0; u < d; ++u) r += a[u] < k ? 1u : 0u;
+            put_rank(info, eid, col, dc, row, p0 + t, r);
+        }
+        return;
+    }
+    int len2 = 1;
+    while (len2 < d) len2 <<= 1;
+    for (int t = threadIdx.x; t < len2; t += blockDim.x)
+        a[t] = t < d ? (((unsigned long long)ekey[p0 + t] << 32) | (unsigned)t) : ~0ull;
+    __syncthreads();
+    block_bitonic(a, len2);
+    for (int t = threadIdx.x; t < d; t += blockDim.x)
+        put_rank(info, eid, col, dc, row, p0 + (int64_t)(a[t] & 0xffffffffull), (uint32_t)t);
 }
 
 // rows of degree > kSortCap: one CTA per (row, chunk of kSortCap entries) sorts
@@ -500,7 +512,7 @@ static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, i
         AD_TRY(dalloc_t(g, n_mid, &rows));
         AD_TRY(dalloc_t(g, n_mid, &chunk));
         AD_LAUNCH(k_chunk_expand, g->num_sms * 8, 256, 0, g->stream, nmid, fmid, n, rows, chunk);
-        AD_LAUNCH(k_rank_mid, (int)n_mid, 128, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows, ekey, info);
+        AD_LAUNCH(k_rank_mid, (int)n_mid, 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows, ekey, info);
         AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
         dfree(g, rows);
         dfree(g, chunk);

@@ -94,6 +94,7 @@ ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, 
     a.stride = cf.stride; a.nchunks = cf.nchunks; a.R = R;
     a.omega = (float)omega;
     a.voff = g->voff; a.G = g->G; a.blocked = g->G > 1 ? 1 : 0;
+    a.anchor = g->anchor;
     fill_plan(a, *sp);
     a.x_in = x_in; a.x_out = x_out;
     a.mm_prev_min = pmin; a.mm_prev_max = pmax; a.mm_min = mn; a.mm_max = mx;
@@ -103,10 +104,11 @@ ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, 
 ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, uint64_t seed,
                              uint32_t stream_id, ad_storage storage, int32_t flags, float *rho_dev,
                              const KeepSpec *keep) {
+    if (g->m == 0) return AD_OK;   // no edges: nothing to relax and no distance to write
     const Config cf = pick_config(R, storage);
     const int groups = 32 / cf.lpr;
     const size_t esz = storage == AD_STORAGE_FP32 ? 4 : 2;
-    const size_t xbytes = (size_t)g->n * cf.stride * esz + 256;
+    const size_t xbytes = ((size_t)g->n + 1) * cf.stride * esz;
     AD_TRY(ensure(g, g->x0, xbytes));
     AD_TRY(ensure(g, g->x1, xbytes));
     const size_t mm_words = (size_t)(k > 0 ? k : 1) * g->G * cf.stride;
@@ -146,6 +148,7 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
     a.voff = g->voff;
     a.G = g->G;
     a.blocked = g->G > 1 ? 1 : 0;
+    a.anchor = g->anchor;
 
     void *xin = g->x0.ptr, *xout = g->x1.ptr;
     const size_t smem = 2 * 8 * (size_t)cf.stride * sizeof(float);

@@ -4,24 +4,48 @@
 //
 // Data layout: the R test vectors of vertex i form row i of X[n][stride]
 // (stride = lanes_per_row * chunks_per_lane * V elements, 16-byte chunks,
-// V = 4 FP32 or 8 BF16 values).  A lane group of LPR lanes owns one row at a
+// V = 4 FP32 or 8 16-bit values).  A lane group of LPR lanes owns one row at a
 // time; lane gl of the group holds chunks gl, gl + LPR, ... of the row.
 //
-// Rescale.  Sweep t stores the raw update z = (1-omega) y_i + omega D_i^-1 sum_j
-// w_ij y_j applied to the stored values y of sweep t-1, mapped through the
-// affine x = a y + b that rescales sweep t-1 to [-1/2, 1/2]:
-//     sum_j w_ij (a y_j + b) = a sum_j w_ij y_j + b D_i,
-// so the stored value of sweep t is a z + b (the JOR operator commutes with
-// per-vector affine maps).  Each sweep reduces min/max of what it stores; the
-// next launch turns them into (a, b).  The distance of Alg. 1 uses the last
-// affine: rho = sqrt(sum_r a_r^2 (y_i^r - y_j^r)^2).
+// Stored frame.  The iterate of Alg. 1 after sweep t is x_t = rescale(M x_{t-1}),
+// M = (1-omega) I + omega D^-1 W, rescale mapping [min, max] of each vector
+// onto [-1/2, 1/2].  M commutes with adding a constant vector and with scaling,
+// and rescale ignores both, so the kernels store
+//     s_t = a_{t-1} (M s_{t-1} - s_{t-1}[anchor]),   a_{t-1} = 1 / (max - min)(s_{t-1}),
+// which differs from x_t by a per-vector shift only: the same rescaled values,
+// the same distances rho = a_t |s_i - s_j|.  The anchor is the vertex of
+// largest weighted degree of each graph.  Its value lies inside the bulk of
+// the smoothed vector, so the stored values are deviations around zero instead
+// of a common offset plus small deviations -- which is what lets 16-bit
+// storage resolve the small distances of well-mixed graphs.  Each sweep
+// reduces min/max of what it stores; the next launch turns them into a.
 #pragma once
 #include "ad_internal.cuh"
 
 #include <cmath>
 #include <cstring>
 
+// Tuning parameters (compile-time; the defaults are the measured choice on GB300).
+#ifndef AD_SWEEP_UB
+#define AD_SWEEP_UB 4          // independent row loads in flight per lane
+#endif
+#ifndef AD_SWEEP_MINB
+#define AD_SWEEP_MINB 4        // minimum resident CTAs per SM requested from ptxas
+#endif
+#ifndef AD_COL_STREAM
+#define AD_COL_STREAM 1        // 1: read column indices with the streaming (evict-first) hint
+#endif
+
 namespace ad {
+
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T *p) {
+#if AD_COL_STREAM
+    return __ldcs(p);
+#else
+    return __ldg(p);
+#endif
+}
 
 struct SweepArgs {
     const int64_t *rp;
@@ -53,6 +77,7 @@ struct SweepArgs {
     const int64_t *voff;
     int32_t G;
     int32_t blocked;
+    const int32_t *anchor;   // [G] vertex whose previous value is subtracted (the stored frame's centre)
 };
 
 __device__ __forceinline__ int graph_of(const int64_t *voff, int G, int64_t row) {
@@ -133,7 +158,7 @@ __device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int6
     using L = Lane<T, LPR, CPL>;
     constexpr int V = L::V, G = L::G;
     constexpr int U = 32 / G;                       // neighbours per group per batch of 32
-    constexpr int UB = (8 / CPL) < U ? (8 / CPL) : U;   // loads in flight per chunk slot
+    constexpr int UB = (AD_SWEEP_UB / CPL) < U ? (AD_SWEEP_UB / CPL) : U;   // loads in flight per chunk slot
     const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
     const int64_t row_q = a.stride / V;   // 16-byte chunks per row
     for (int64_t base = p0; base < p1; base += 32) {
@@ -141,8 +166,8 @@ __device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int6
         int32_t cj = 0;
         float wj = 0.f;
         if (p < p1) {
-            cj = __ldg(a.col + p);
-            wj = a.w ? __ldg(a.w + p) : 1.f;
+            cj = ld_stream(a.col + p);
+            wj = a.w ? ld_stream(a.w + p) : 1.f;
         }
         const int cnt = (int)(p1 - base < 32 ? p1 - base : 32);
 #pragma unroll
@@ -176,7 +201,7 @@ __device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int6
 
 // Gather-accumulate a short row (<= kSmallUnroll entries per round) with one
 // lane group: all of its column indices, then all row loads, then the sums.
-constexpr int kSmallUnroll = 8;
+constexpr int kSmallUnroll = AD_SWEEP_UB;
 template <typename T, int LPR, int CPL>
 __device__ __forceinline__ void group_gather(const SweepArgs &a, int64_t p0, int64_t p1, int gl,
                                              float (&acc)[CPL * Store<T>::V]) {
@@ -190,8 +215,8 @@ __device__ __forceinline__ void group_gather(const SweepArgs &a, int64_t p0, int
 #pragma unroll
         for (int u = 0; u < UB; ++u) {
             const bool ok = base + u < p1;
-            nb[u] = ok ? __ldg(a.col + base + u) : 0;
-            wt[u] = ok ? (a.w ? __ldg(a.w + base + u) : 1.f) : 0.f;
+            nb[u] = ok ? ld_stream(a.col + base + u) : 0;
+            wt[u] = ok ? (a.w ? ld_stream(a.w + base + u) : 1.f) : 0.f;
         }
         uint4 v[UB][CPL];
 #pragma unroll
@@ -222,15 +247,25 @@ __device__ __forceinline__ void reduce_groups(float (&acc)[E]) {
         for (int e = 0; e < E; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], off);
 }
 
-// Epilogue of a row: z = (1-omega) y_i + omega Dinv_i S, store a z + b, track min/max.
+// Epilogue of a row: z = (1-omega) s_i + omega Dinv_i S, store a (z - c), track min/max.
 template <typename T, int LPR, int CPL>
-__device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, int gl,
+__device__ __forceinline__ void load_own(const SweepArgs &a, int64_t row, int gl, uint4 (&own)[CPL]) {
+    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
+    const int64_t row_q = a.stride / Store<T>::V;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        const int q = gl + c * LPR;
+        own[c] = q < a.nchunks ? __ldg(X + row * row_q + q) : make_uint4(0, 0, 0, 0);
+    }
+}
+
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, int gl, const uint4 (&own)[CPL],
                                              const float (&S)[CPL * Store<T>::V],
                                              const float (&A)[CPL * Store<T>::V],
-                                             const float (&B)[CPL * Store<T>::V],
+                                             const float (&C)[CPL * Store<T>::V],
                                              float (&mn)[CPL * Store<T>::V], float (&mx)[CPL * Store<T>::V]) {
     constexpr int V = Store<T>::V;
-    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
     uint4 *Y = reinterpret_cast<uint4 *>(a.x_out);
     const int64_t row_q = a.stride / V;
     const float dinv = __ldg(a.Dinv + row);
@@ -240,11 +275,11 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, in
         const int q = gl + c * LPR;
         if (q < a.nchunks) {
             float y[V], o[V];
-            Store<T>::unpack(__ldg(X + row * row_q + q), y);
+            Store<T>::unpack(own[c], y);
 #pragma unroll
             for (int e = 0; e < V; ++e) {
                 const float z = fmaf(om1, y[e], om * (S[c * V + e] * dinv));
-                o[e] = Store<T>::round(fmaf(A[c * V + e], z, B[c * V + e]));
+                o[e] = Store<T>::round(A[c * V + e] * (z - C[c * V + e]));
                 mn[c * V + e] = fminf(mn[c * V + e], o[e]);
                 mx[c * V + e] = fmaxf(mx[c * V + e], o[e]);
             }
@@ -253,10 +288,11 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, in
     }
 }
 
-// Affine (a, b) of the previous sweep's rescale for the lane's elements.
+// Scale a = 1 / (max - min) of the previous sweep's stored values for the
+// lane's elements (1 before the first sweep, 0 for a vector with max == min).
 template <typename T, int LPR, int CPL>
-__device__ __forceinline__ void load_affine(const uint32_t *pmin, const uint32_t *pmax, int gl,
-                                            float (&A)[CPL * Store<T>::V], float (&B)[CPL * Store<T>::V]) {
+__device__ __forceinline__ void load_scale(const uint32_t *pmin, const uint32_t *pmax, int gl,
+                                           float (&A)[CPL * Store<T>::V]) {
     // pmin / pmax point at the slots of the row's graph (nullptr: no rescale yet)
     constexpr int V = Store<T>::V;
 #pragma unroll
@@ -264,21 +300,31 @@ __device__ __forceinline__ void load_affine(const uint32_t *pmin, const uint32_t
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             const int r = (gl + c * LPR) * V + e;
-            float av = 1.f, bv = 0.f;
+            float av = 1.f;
             if (pmin) {
                 const double lo = ord2f(pmin[r]), hi = ord2f(pmax[r]);
-                if (hi > lo) {
-                    const double s = 1.0 / (hi - lo);
-                    av = (float)s;
-                    bv = (float)(-lo * s - 0.5);
-                } else {
-                    av = 0.f;
-                    bv = 0.f;
-                }
+                av = hi > lo ? (float)(1.0 / (hi - lo)) : 0.f;
             }
             A[c * V + e] = av;
-            B[c * V + e] = bv;
         }
+}
+
+// Centre c of the stored frame: the previous values of the graph's anchor vertex.
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void load_center(const SweepArgs &a, int g, int gl, float (&C)[CPL * Store<T>::V]) {
+    constexpr int V = Store<T>::V;
+    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
+    const int64_t row = a.anchor[g];
+    const int64_t row_q = a.stride / V;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        const int q = gl + c * LPR;
+        if (q < a.nchunks) Store<T>::unpack(__ldg(X + row * row_q + q), C + c * V);
+        else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) C[c * V + e] = 0.f;
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -288,7 +334,7 @@ __device__ __forceinline__ void load_affine(const uint32_t *pmin, const uint32_t
 template <typename T, int LPR, int CPL>
 struct LaneStats {
     static constexpr int V = Store<T>::V, E = CPL * V;
-    float A[E], B[E], mn[E], mx[E];
+    float A[E], C[E], mn[E], mx[E];
     int cg = -1;
 
     __device__ __forceinline__ void flush(const SweepArgs &a, int gl) {
@@ -304,13 +350,14 @@ struct LaneStats {
                 }
             }
     }
-    // make the lane's state describe graph `g` (affine of its previous sweep)
+    // make the lane's state describe graph `g` (scale and centre from its previous sweep)
     __device__ __forceinline__ void enter(const SweepArgs &a, int gl, int g, bool flush_old) {
         if (g == cg) return;
         if (flush_old) flush(a, gl);
         cg = g;
-        load_affine<T, LPR, CPL>(a.mm_prev_min ? a.mm_prev_min + (size_t)g * a.stride : nullptr,
-                                 a.mm_prev_max ? a.mm_prev_max + (size_t)g * a.stride : nullptr, gl, A, B);
+        load_scale<T, LPR, CPL>(a.mm_prev_min ? a.mm_prev_min + (size_t)g * a.stride : nullptr,
+                                a.mm_prev_max ? a.mm_prev_max + (size_t)g * a.stride : nullptr, gl, A);
+        load_center<T, LPR, CPL>(a, g, gl, C);
 #pragma unroll
         for (int e = 0; e < E; ++e) { mn[e] = INFINITY; mx[e] = -INFINITY; }
     }
@@ -320,7 +367,7 @@ struct LaneStats {
 // One JOR sweep (Alg. 1 inner loop) over all rows of degree > 0.
 // ----------------------------------------------------------------------------
 template <typename T, int LPR, int CPL>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
+__global__ void __launch_bounds__(256, AD_SWEEP_MINB) k_sweep(SweepArgs a) {
     using L = Lane<T, LPR, CPL>;
     constexpr int V = L::V, E = L::E, G = L::G;
     extern __shared__ float sm[];   // [2][warps][stride]
@@ -365,43 +412,57 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
             old = __shfl_sync(0xffffffffu, old, 0);
             if (old == (uint32_t)(nchunk - 1)) {
                 __threadfence();
-                if (grp == 0) {
-                    float S[E];
+                // group g sums partials g, g + G, ... (fixed order); then the groups' sums are added
+                uint4 own[CPL];
+                load_own<T, LPR, CPL>(a, row, gl, own);
+                float S[E];
 #pragma unroll
-                    for (int e = 0; e < E; ++e) S[e] = 0.f;
-                    for (int32_t cc2 = 0; cc2 < nchunk; ++cc2) {
-                        const float *pp = a.part + (t0 + cc2) * (int64_t)a.stride;
+                for (int e = 0; e < E; ++e) S[e] = 0.f;
+                for (int32_t cc2 = grp; cc2 < nchunk; cc2 += G) {
+                    const float4 *pp = reinterpret_cast<const float4 *>(a.part + (t0 + cc2) * (int64_t)a.stride);
 #pragma unroll
-                        for (int cc = 0; cc < CPL; ++cc) {
-                            const int q = gl + cc * LPR;
-                            if (q < a.nchunks) {
+                    for (int cc = 0; cc < CPL; ++cc) {
+                        const int q = gl + cc * LPR;
+                        if (q < a.nchunks) {
 #pragma unroll
-                                for (int e = 0; e < V; ++e) S[cc * V + e] += __ldcg(pp + q * V + e);
+                            for (int e4 = 0; e4 < V / 4; ++e4) {
+                                const float4 f = __ldcg(pp + (q * V) / 4 + e4);
+                                S[cc * V + 4 * e4 + 0] += f.x;
+                                S[cc * V + 4 * e4 + 1] += f.y;
+                                S[cc * V + 4 * e4 + 2] += f.z;
+                                S[cc * V + 4 * e4 + 3] += f.w;
                             }
                         }
                     }
+                }
+                reduce_groups<LPR, E>(S);
+                if (grp == 0) {
                     ls.enter(a, gl, row_graph(row), true);
-                    row_epilogue<T, LPR, CPL>(a, row, gl, S, ls.A, ls.B, ls.mn, ls.mx);
+                    row_epilogue<T, LPR, CPL>(a, row, gl, own, S, ls.A, ls.C, ls.mn, ls.mx);
                 }
                 if (lane == 0) a.big_counter[t0] = 0u;
             }
         } else if (task < a.n_big + a.n_medium) {
             // ---- one row, whole warp
             const int64_t row = a.medium_row[task - a.n_big];
+            uint4 own[CPL];
+            load_own<T, LPR, CPL>(a, row, gl, own);
             warp_gather<T, LPR, CPL>(a, a.rp[row], a.rp[row + 1], lane, grp, gl, acc);
             reduce_groups<LPR, E>(acc);
             if (grp == 0) {
                 ls.enter(a, gl, row_graph(row), true);
-                row_epilogue<T, LPR, CPL>(a, row, gl, acc, ls.A, ls.B, ls.mn, ls.mx);
+                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.A, ls.C, ls.mn, ls.mx);
             }
         } else {
             // ---- G low-degree rows, one per lane group
             const int64_t si = (task - a.n_big - a.n_medium) * G + grp;
             if (si < a.n_small_rows) {
                 const int64_t row = a.small_row[si];
+                uint4 own[CPL];
+                load_own<T, LPR, CPL>(a, row, gl, own);
                 group_gather<T, LPR, CPL>(a, a.rp[row], a.rp[row + 1], gl, acc);
                 ls.enter(a, gl, row_graph(row), true);
-                row_epilogue<T, LPR, CPL>(a, row, gl, acc, ls.A, ls.B, ls.mn, ls.mx);
+                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.A, ls.C, ls.mn, ls.mx);
             }
         }
     }
@@ -465,6 +526,7 @@ template <typename T, int LPR, int CPL>
 __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64_t p0, int64_t p1, int step,
                                           int first, int gl, unsigned gmask, const float (&A2)[CPL * Store<T>::V]) {
     constexpr int V = Store<T>::V, E = CPL * V;
+    constexpr int UB = AD_SWEEP_UB;     // edges of one group in flight
     const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
     const int64_t row_q = a.stride / V;
     float yi[E];
@@ -480,47 +542,62 @@ __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64
     const int64_t ebase = a.eoff[row] - a.upos[row];
     const double Di = a.normalize ? a.D[row] : 0.0;
     // the lanes of one group share p, so the group-masked reduction below is uniform
-    for (int64_t p = p0 + first; p < p1; p += step) {
-        const int32_t j = __ldg(a.col + p);
-        float s = 0.f;
+    for (int64_t pb = p0 + first; pb < p1; pb += (int64_t)step * UB) {
+        int32_t jn[UB];
+        uint4 v[UB][CPL];
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int q = gl + c * LPR;
-            if (q < a.nchunks) {
+        for (int u = 0; u < UB; ++u) {
+            const int64_t p = pb + (int64_t)u * step;
+            jn[u] = p < p1 ? ld_stream(a.col + p) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                const int q = gl + c * LPR;
+                v[u][c] = (pb + (int64_t)u * step < p1 && q < a.nchunks) ? __ldg(X + (int64_t)jn[u] * row_q + q)
+                                                                          : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int64_t p = pb + (int64_t)u * step;
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
                 float yj[V];
-                Store<T>::unpack(__ldg(X + (int64_t)j * row_q + q), yj);
+                Store<T>::unpack(v[u][c], yj);
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
                     const float d = yi[c * V + e] - yj[e];
                     s = fmaf(A2[c * V + e] * d, d, s);
                 }
             }
-        }
 #pragma unroll
-        for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
-        if (gl == 0) {
-            float rho = sqrtf(s);
-            if (a.normalize) rho = (float)((double)rho * sqrt(Di * a.D[j]));
-            a.rho[ebase + p] = rho;
+            for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
+            if (gl == 0 && p < p1) {
+                float rho = sqrtf(s);
+                if (a.normalize) rho = (float)((double)rho * sqrt(Di * a.D[jn[u]]));
+                a.rho[ebase + p] = rho;
+            }
         }
     }
 }
 
 template <typename T, int LPR, int CPL>
-__global__ void __launch_bounds__(256) k_distance(SweepArgs a) {
+__global__ void __launch_bounds__(256, AD_SWEEP_MINB) k_distance(SweepArgs a) {
     using L = Lane<T, LPR, CPL>;
     constexpr int V = L::V, E = L::E, G = L::G;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int grp = lane / LPR, gl = lane % LPR;
     const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (grp * LPR));
-    float A[E], B[E], A2[E];
+    float A[E], A2[E];
     int cg = -1;
     // squared scale of the last rescale of graph g; padded vectors r >= R excluded
     auto enter = [&](int g) {
         if (g == cg) return;
         cg = g;
-        load_affine<T, LPR, CPL>(a.mm_prev_min ? a.mm_prev_min + (size_t)g * a.stride : nullptr,
-                                 a.mm_prev_max ? a.mm_prev_max + (size_t)g * a.stride : nullptr, gl, A, B);
+        load_scale<T, LPR, CPL>(a.mm_prev_min ? a.mm_prev_min + (size_t)g * a.stride : nullptr,
+                                a.mm_prev_max ? a.mm_prev_max + (size_t)g * a.stride : nullptr, gl, A);
 #pragma unroll
         for (int c = 0; c < CPL; ++c)
 #pragma unroll
