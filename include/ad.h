@@ -269,6 +269,31 @@ ad_status ad_sparsify_scores(ad_graph_t g, const float *score, double fraction, 
 ad_status ad_select_per_node(ad_graph_t g, const float *score, double e, ad_mode mode, uint8_t *keep_out,
                              int64_t *n_kept);
 
+/*
+ * Whole-graph ranking (as ad_sparsify_scores with AD_SCOPE_WHOLE_GRAPH on a
+ * single graph whose edge ids are 0..m-1) for callers that cannot let a
+ * library allocate device memory -- a process whose device memory is all
+ * pre-reserved by its own allocator or arena, or a latency-critical service
+ * that must not reach the allocator on its request path.  The paper has no
+ * counterpart; this is an operational variant.
+ * score[m] (FP32, >= 0, finite) and keep[m] (uint8 output) must be device
+ * arrays; K = floor(fraction m + 1/2) edges are kept in the order of mode
+ * (ties by index); *n_kept (may be NULL) receives K.  stream: a cudaStream_t.
+ * No cudaMalloc, cudaFree or allocating library routine is called: all
+ * scratch lives in one fixed device array of about 600 KB that every GPU
+ * loading the library holds until exit, which limits m to 2^26
+ * (AD_ERR_INVALID_ARG beyond).  The first call on a device looks the array
+ * up (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls on a device share the array: each call rewrites what it reads, and
+ * calls that overlap on the GPU race, so the caller must order them.  The
+ * call waits for its score check (one small device-to-host copy); the
+ * selection itself is queued on stream and complete after the stream is
+ * synchronised.  Errors: AD_ERR_INVALID_ARG (size, fraction, mode, host
+ * pointers, negative or non-finite scores), AD_ERR_CUDA.
+ */
+ad_status ad_select_whole_graph_noalloc(const float *score, int64_t m, double fraction, ad_mode mode, uint8_t *keep,
+                                        int64_t *n_kept, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Multilevel sparsification (Sec. 5, Alg. 6)                                */
 /* ------------------------------------------------------------------------ */

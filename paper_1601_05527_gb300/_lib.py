@@ -71,6 +71,7 @@ _SIGS = {
     "ad_sparsify": (ctypes.c_int, [_VP, _D, ctypes.c_int, ctypes.c_int, _VP, _PI64, _PD]),
     "ad_sparsify_scores": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, ctypes.c_int, _VP, _PI64, _PD]),
     "ad_select_per_node": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, _VP, _PI64]),
+    "ad_select_whole_graph_noalloc": (ctypes.c_int, [_VP, _I64, _D, ctypes.c_int, _VP, _PI64, _VP]),
     "ad_ml_build": (ctypes.c_int, [_VP, ctypes.POINTER(ad_ml_params), ctypes.POINTER(_VP)]),
     "ad_ml_levels": (ctypes.c_int, [_VP, _PI32]),
     "ad_ml_level_size": (ctypes.c_int, [_VP, _I32, _PI64, _PI64]),
@@ -297,6 +298,15 @@ def ad_select_per_node(g, score, e, mode, keep_out):
     s, k = _Arr(score, np.float32), _Arr(keep_out, np.uint8)
     nk = ctypes.c_int64()
     _check(load().ad_select_per_node(g, s.ptr, float(e), MODES.get(mode, mode), k.ptr, ctypes.byref(nk)))
+    return nk.value
+
+
+def ad_select_whole_graph_noalloc(score, m, fraction, mode, keep_out, stream=None):
+    """Whole-graph ranking with no device allocation (device score/keep arrays)."""
+    s, k = _Arr(score, np.float32), _Arr(keep_out, np.uint8)
+    nk = ctypes.c_int64()
+    _check(load().ad_select_whole_graph_noalloc(s.ptr, int(m), float(fraction), MODES.get(mode, mode), k.ptr,
+                                                ctypes.byref(nk), _stream_ptr(stream)))
     return nk.value
 
 

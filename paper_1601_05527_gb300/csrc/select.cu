@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 namespace ad {
 
@@ -663,3 +664,152 @@ ad_status check_scores(ad_graph_t g, const float *score) {
 }
 
 }  // namespace ad
+
+// ----------------------------------------------------------------------------
+// Whole-graph selection that allocates nothing (ad_select_whole_graph_noalloc).
+//
+// Some callers cannot let a library allocate device memory: a process whose
+// device memory is entirely pre-reserved by its own allocator or arena (where
+// a foreign cudaMalloc would fail or fragment it), or a latency-critical
+// service that must not hit the allocator on its request path.  For them the
+// radix select above runs with all of its scratch -- selection state, the
+// three digit histograms, the tile list and the per-tile tie counts -- in one
+// fixed file-scope device array sized for at most kNoAllocMaxEdges edges.
+// Every GPU that loads this library holds that array until the process exits.
+// All calls on a device share it and it keeps the previous call's contents, so
+// each call first rewrites everything it reads; calls whose work overlaps on
+// the GPU (two streams, or two host threads) race on it and must be ordered by
+// the caller.
+// ----------------------------------------------------------------------------
+namespace ad {
+
+constexpr int64_t kNoAllocMaxEdges = (int64_t)1 << 26;
+constexpr int64_t kNoAllocMaxTiles = kNoAllocMaxEdges / kTile;
+constexpr int kNoAllocMaxDevices = 64;
+
+struct NoAllocScratch {
+    SelState st;
+    unsigned long long bad;
+    int32_t first_tile[2];
+    uint32_t hist[3 * 2048];
+    int32_t tg[kNoAllocMaxTiles];
+    int64_t ts[kNoAllocMaxTiles];
+    int64_t te[kNoAllocMaxTiles];
+    int64_t ties[kNoAllocMaxTiles];
+    int64_t tie_off[kNoAllocMaxTiles];
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+static std::mutex g_noalloc_mu;
+static NoAllocScratch *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+static ad_status noalloc_scratch(NoAllocScratch **out) {
+    int dev = 0;
+    AD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(AD_ERR_INVALID_ARG, "device id out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(AD_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = static_cast<NoAllocScratch *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return AD_OK;
+}
+
+// Rewrites every scratch field a call reads: state, histograms, tile list.
+__global__ void k_noalloc_init(NoAllocScratch *s, int64_t m, int64_t K, int64_t ntiles) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * 2048; t += stride) s->hist[t] = 0;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < ntiles; b += stride) {
+        s->tg[b] = 0;
+        s->ts[b] = b * kTile;
+        s->te[b] = (b + 1) * kTile < m ? (b + 1) * kTile : m;
+        s->ties[b] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s->st.prefix = 0;
+        s->st.pad = 0;
+        s->st.K = K;
+        s->st.m = m;
+        s->st.k_rem = (K > 0 && K < m) ? K : 0;
+        s->bad = ~0ull;
+        s->first_tile[0] = 0;
+        s->first_tile[1] = (int32_t)ntiles;
+    }
+}
+
+// Exclusive scan of at most kNoAllocMaxTiles values by one CTA of 1024 threads.
+__global__ void k_noalloc_scan(const int64_t *in, int64_t *out, int64_t n) {
+    __shared__ int64_t sh[32];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = (int64_t)threadIdx.x * per;
+    int64_t local = 0;
+    for (int64_t i = b0; i < b0 + per && i < n; ++i) local += in[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t v = lane < nw ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane < nw) sh[lane] = v;
+    }
+    __syncthreads();
+    int64_t run = (warp > 0 ? sh[warp - 1] : 0) + x - local;
+    for (int64_t i = b0; i < b0 + per && i < n; ++i) {
+        out[i] = run;
+        run += in[i];
+    }
+}
+
+}  // namespace ad
+
+extern "C" ad_status ad_select_whole_graph_noalloc(const float *score, int64_t m, double fraction, ad_mode mode,
+                                                   uint8_t *keep, int64_t *n_kept, void *stream) {
+    using namespace ad;
+    if (m < 0 || m > kNoAllocMaxEdges)
+        return fail(AD_ERR_INVALID_ARG, "m = " + std::to_string(m) + " exceeds the fixed scratch limit of " +
+                                            std::to_string(kNoAllocMaxEdges) + " edges");
+    if (!(fraction >= 0.0 && fraction <= 1.0)) return fail(AD_ERR_INVALID_ARG, "fraction must be in [0, 1]");
+    if (mode != AD_MODE_LOCAL && mode != AD_MODE_GLOBAL) return fail(AD_ERR_INVALID_ARG, "bad mode");
+    if (m > 0 && (!is_device_ptr(score) || !is_device_ptr(keep)))
+        return fail(AD_ERR_INVALID_ARG, "score and keep must be device arrays (nothing is staged)");
+    NoAllocScratch *s = nullptr;
+    AD_TRY(noalloc_scratch(&s));
+    const int64_t K = target_count(m, fraction);
+    if (n_kept) *n_kept = K;
+    if (m == 0) return AD_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int desc = mode == AD_MODE_GLOBAL ? 1 : 0;
+    const int64_t ntiles = (m + kTile - 1) / kTile;
+    AD_LAUNCH(k_noalloc_init, 64, 256, 0, st, s, m, K, ntiles);
+    AD_LAUNCH(k_check_scores, 152 * 8, 256, 0, st, score, m, &s->bad);
+    unsigned long long bad = 0;
+    AD_CUDA_TRY(cudaMemcpyAsync(&bad, &s->bad, sizeof(bad), cudaMemcpyDeviceToHost, st));
+    AD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad != ~0ull) return fail(AD_ERR_INVALID_ARG, "score " + std::to_string(bad) + " is negative or not finite");
+    const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
+    const uint32_t hi_masks[3] = {0u, 0xFFE00000u, 0xFFFFFC00u};
+    for (int pass = 0; pass < 3; ++pass) {
+        AD_LAUNCH(k_sel_hist, (int)ntiles, 256, 0, st, score, desc, s->tg, s->ts, s->te, &s->st, shifts[pass],
+                  bits[pass], hi_masks[pass], s->hist + pass * 2048);
+        AD_LAUNCH(k_sel_find, 1, 256, 0, st, s->hist + pass * 2048, &s->st, shifts[pass], bits[pass]);
+    }
+    AD_LAUNCH(k_sel_ties, (int)ntiles, 256, 0, st, score, desc, s->tg, s->ts, s->te, &s->st, s->ties);
+    AD_LAUNCH(k_noalloc_scan, 1, 1024, 0, st, s->ties, s->tie_off, ntiles);
+    AD_LAUNCH(k_sel_write, (int)ntiles, kTileThreads, 0, st, score, desc, s->tg, s->ts, s->te, &s->st, s->tie_off,
+              s->first_tile, keep);
+    return AD_OK;
+}

@@ -1,0 +1,51 @@
+"""The allocation-free whole-graph selection, ad_select_whole_graph_noalloc.
+
+It serves callers that cannot let a library allocate device memory -- a
+process whose device memory is pre-reserved by its own arena, or a
+latency-critical service that must not reach the allocator -- by keeping its
+scratch in one fixed device array.  Checked through the C ABI against the
+allocating entry point (ad_sparsify_scores, whole-graph scope) on identical
+scores, bit for bit, for two calls in a row: the second call must not be
+affected by what the first left in the shared scratch."""
+import numpy as np
+import pytest
+
+from paper_1601_05527_gb300 import graphgen
+from gpu_util import lib
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_matches_allocating_entry_point_on_two_calls():
+    import torch
+    L = lib()
+    g = graphgen.rmat(14, 16, seed=5)
+    s_np = graphgen.random_scores(g.m, 1000, seed=3)          # ties included
+    dev = torch.device("cuda")
+    score = torch.from_numpy(s_np).to(dev)
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
+    for mode, f in (("local", 0.3), ("global", 0.55)):
+        ref = np.zeros(g.m, np.uint8)
+        ref_kept, _ = L.ad_sparsify_scores(h, s_np, f, mode, "whole_graph", ref)
+        keep = torch.full((g.m,), 7, dtype=torch.uint8, device=dev)   # stale output contents
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        kept = L.ad_select_whole_graph_noalloc(score, g.m, f, mode, keep)
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == before
+        np.testing.assert_array_equal(keep.cpu().numpy(), ref)
+        assert kept == ref_kept == int(ref.sum())
+    L.ad_graph_destroy(h)
+
+
+def test_noalloc_rejects_oversize_and_host_arrays():
+    import torch
+    L = lib()
+    dev = torch.device("cuda")
+    score = torch.zeros(16, dtype=torch.float32, device=dev)
+    keep = torch.zeros(16, dtype=torch.uint8, device=dev)
+    with pytest.raises(L.ADError) as ei:
+        L.ad_select_whole_graph_noalloc(score, (1 << 26) + 1, 0.5, "local", keep)
+    assert ei.value.status == 1 and "limit" in str(ei.value)
+    with pytest.raises(L.ADError):
+        L.ad_select_whole_graph_noalloc(np.zeros(16, np.float32), 16, 0.5, "local", keep)
