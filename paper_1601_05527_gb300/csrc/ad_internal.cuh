@@ -270,6 +270,7 @@ struct ad_graph_s {
     // scores of the last ad_algebraic_distance call
     float *rho = nullptr;
     bool have_rho = false;
+    uint64_t rho_version = 0;    // bumped whenever rho is recomputed
 
     // cached scratch
     ad::DevBuf x0, x1, part, mm, ws;
@@ -283,6 +284,11 @@ struct ad_graph_s {
     // state kept for the backward pass
     struct Saved;
     Saved *saved = nullptr;
+
+    // cached selection workspace (select.cu) and scan workspace (graph.cu)
+    struct SelCache;
+    SelCache *sel = nullptr;
+    ad::DevBuf scan_ws;
 };
 
 namespace ad {
@@ -339,6 +345,7 @@ ad_status select_per_node_at(ad_graph_t g, const float *score_dev, double e, ad_
                              uint8_t *keep_dev, int64_t *n_kept);
 
 ad_status check_scores(ad_graph_t g, const float *score);
+void free_sel_cache(ad_graph_t g);
 
 // sorting and compaction (sort.cu)
 ad_status radix_sort_pairs(ad_graph_t g, uint64_t *keys, int64_t *vals, int64_t n, const std::vector<int> &shifts);

@@ -183,6 +183,7 @@ namespace ad {
 static void destroy_graph(ad_graph_t g) {
     if (!g) return;
     if (g->saved) free_saved(g);
+    free_sel_cache(g);
     for (auto &b : g->owned) release(g, b);
     g->owned.clear();
     cudaStreamSynchronize(g->stream);
@@ -327,6 +328,7 @@ extern "C" ad_status ad_graph_set_edge_weights(ad_graph_t g, const float *w_edge
     if (b != ~0ull) return fail(AD_ERR_BAD_WEIGHT, "edge weight " + std::to_string(b) + " not positive and finite");
     AD_TRY(recompute_degrees(g));
     g->have_rho = false;
+    g->rho_version++;
     return AD_OK;
 }
 
@@ -345,9 +347,11 @@ extern "C" ad_status ad_algebraic_distance(ad_graph_t g, int32_t R, int32_t k, d
         return fail(AD_ERR_INVALID_ARG, "kept state needs FP32 storage and no normalisation");
     if (!g->rho) AD_TRY(dalloc_t(g, g->m + 1, &g->rho));
     g->have_rho = false;
+    g->rho_version++;
     if (flags & AD_DIST_KEEP_STATE) AD_TRY(algebraic_distance_keep(g, R, k, omega, seed, stream_id, g->rho));
     else AD_TRY(algebraic_distance(g, R, k, omega, seed, stream_id, storage, flags, g->rho));
     g->have_rho = true;
+    g->rho_version++;
     if (rho_out) AD_TRY(copy_out(g, rho_out, g->rho, g->m * sizeof(float)));
     return AD_OK;
 }

@@ -67,37 +67,37 @@ __global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *tile_prefix) 
     if (i < n) out[i] += tile_prefix[i / kScanTile];
 }
 
+// Scan of n values with the tile sums of every level carved from ws.
+static ad_status scan_rec(ad_graph_t g, const int64_t *in, int64_t *out, int64_t n, int64_t *ws) {
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    int64_t *sums = ws, *pref = ws + tiles + 1;
+    AD_LAUNCH(k_scan_tiles, (int)tiles, kScanThreads, 0, g->stream, in, out, n, sums);
+    if (tiles > 1) {
+        AD_TRY(scan_rec(g, sums, pref, tiles, ws + 2 * (tiles + 1)));
+        AD_LAUNCH(k_scan_add, (int)((n + 255) / 256), 256, 0, g->stream, out, n, pref);
+    }
+    return AD_OK;
+}
+
 // out[0..n) = exclusive scan of in; *total_host (optional) = sum (synchronises).
+// Scratch comes from a workspace cached in the handle.
 ad_status exclusive_scan_i64(ad_graph_t g, const int64_t *in, int64_t *out, int64_t n, int64_t *total_host) {
     if (n <= 0) {
         if (total_host) *total_host = 0;
         return AD_OK;
     }
-    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    int64_t *sums = nullptr, *pref = nullptr;
-    AD_TRY(dalloc_t(g, tiles + 1, &sums));
-    ad_status st = AD_OK;
-    do {
-        AD_LAUNCH(k_scan_tiles, (int)tiles, kScanThreads, 0, g->stream, in, out, n, sums);
-        if (tiles > 1) {
-            st = dalloc_t(g, tiles + 1, &pref);
-            if (st != AD_OK) break;
-            st = exclusive_scan_i64(g, sums, pref, tiles, nullptr);
-            if (st != AD_OK) break;
-            AD_LAUNCH(k_scan_add, (int)((n + 255) / 256), 256, 0, g->stream, out, n, pref);
-        }
-        if (total_host) {
-            int64_t last_in = 0, last_out = 0;
-            st = copy_out(g, &last_in, in + n - 1, sizeof(int64_t));
-            if (st != AD_OK) break;
-            st = copy_out(g, &last_out, out + n - 1, sizeof(int64_t));
-            if (st != AD_OK) break;
-            *total_host = last_in + last_out;
-        }
-    } while (0);
-    if (pref) dfree(g, pref);
-    dfree(g, sums);
-    return st;
+    size_t words = 0;
+    for (int64_t len = n; len > 1; len = (len + kScanTile - 1) / kScanTile) words += 2 * ((len + kScanTile - 1) / kScanTile + 1);
+    words += 4;
+    AD_TRY(ensure(g, g->scan_ws, words * sizeof(int64_t)));
+    AD_TRY(scan_rec(g, in, out, n, static_cast<int64_t *>(g->scan_ws.ptr)));
+    if (total_host) {
+        int64_t last_in = 0, last_out = 0;
+        AD_TRY(copy_out(g, &last_in, in + n - 1, sizeof(int64_t)));
+        AD_TRY(copy_out(g, &last_out, out + n - 1, sizeof(int64_t)));
+        *total_host = last_in + last_out;
+    }
+    return AD_OK;
 }
 
 // ----------------------------------------------------------------------------
@@ -233,10 +233,21 @@ __global__ void k_entry_eids(const int32_t *col, const int32_t *erow, const int6
 
 // anchor of each graph: the vertex of largest weighted degree, ties to the smaller id
 __global__ void k_anchor_max(const double *D, const int64_t *voff, int G, int64_t n, unsigned long long *best) {
+    unsigned long long mine = 0;   // D >= 0: bit patterns order like the values
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int g = 0;
-        if (G > 1) { int lo = 0, hi = G; while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (voff[mid] <= i) lo = mid; else hi = mid; } g = lo; }
-        atomicMax(best + g, (unsigned long long)__double_as_longlong(D[i]));   // D >= 0: bits order like values
+        const unsigned long long b = (unsigned long long)__double_as_longlong(D[i]);
+        if (G > 1) {
+            int lo = 0, hi = G;
+            while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (voff[mid] <= i) lo = mid; else hi = mid; }
+            atomicMax(best + lo, b);
+        } else if (b > mine) {
+            mine = b;
+        }
+    }
+    if (G == 1) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine = max(mine, __shfl_xor_sync(0xffffffffu, mine, o));
+        if ((threadIdx.x & 31) == 0 && mine) atomicMax(best, mine);
     }
 }
 __global__ void k_anchor_pick(const double *D, const int64_t *voff, int G, int64_t n, const unsigned long long *best,

@@ -567,6 +567,7 @@ extern "C" ad_status ad_ml_build(ad_graph_t g, const ad_ml_params *params, ad_ml
         if ((st = algebraic_distance(cur, p.R, p.k, p.omega, p.seed, (uint32_t)(2 * l), p.storage, 0, cur->rho)) != AD_OK)
             break;
         cur->have_rho = true;
+        cur->rho_version++;
         v.rho = cur->rho;
         if (cur->n <= p.coarsest_n || l + 1 >= p.max_levels) break;      // small enough
         if ((st = dalloc_t(cur, cur->n + 1, &v.agg)) != AD_OK) break;

@@ -78,13 +78,6 @@ static ad_status make_tiles(ad_graph_t g, Tiles &t) {
     AD_TRY(copy_in(g, t.first_tile, t.first_h.data(), (g->G + 1) * sizeof(int32_t)));
     return AD_OK;
 }
-static void free_tiles(ad_graph_t g, Tiles &t) {
-    if (t.graph) dfree(g, t.graph);
-    if (t.start) dfree(g, t.start);
-    if (t.end) dfree(g, t.end);
-    if (t.first_tile) dfree(g, t.first_tile);
-    t = Tiles();
-}
 
 // ----------------------------------------------------------------------------
 // Score validation: every score finite and >= 0.
@@ -247,26 +240,145 @@ __device__ __forceinline__ void put_rank(int4 *info, const int64_t *eid, const i
     else { f[1] = (int)r; f[3] = dc[i]; }
 }
 
-// rows of degree <= 32: one warp each, rank by pairwise comparison
-__global__ void k_rank_small(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc, int64_t n,
-                             const uint32_t *ekey, int4 *info) {
-    const int lane = threadIdx.x & 31;
-    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W) {
-        const int64_t p0 = rp[i];
-        const int d = (int)(rp[i + 1] - p0);
-        if (d == 0 || d > 32) continue;
-        const uint32_t k = lane < d ? ekey[p0 + lane] : 0xffffffffu;
-        uint32_t r = 0;
-        for (int l = 0; l < d; ++l) {
-            const uint32_t o = __shfl_sync(0xffffffffu, k, l);
-            r += (o < k || (o == k && l < lane)) ? 1u : 0u;
+// Both orders from one ascending sort of (key, position): with lt / leq the
+// numbers of entries of the row with key < k / key <= k, the rank of an entry
+// in the descending order (ties still by ascending position) is
+// (d - leq) + (r_asc - lt).
+struct RankOut {
+    int4 *asc, *desc;
+};
+__device__ __forceinline__ void put_ranks(const RankOut &o, const int64_t *eid, const int32_t *col, const int32_t *dc,
+                                          int64_t i, int64_t p, int d, uint32_t r_asc, uint32_t lt, uint32_t leq) {
+    put_rank(o.asc, eid, col, dc, i, p, r_asc);
+    put_rank(o.desc, eid, col, dc, i, p, (uint32_t)d - leq + (r_asc - lt));
+}
+
+constexpr int kSortCap = 2048;      // rows up to this degree are sorted by one CTA
+
+// rows of degree <= GS (8 or 32): a group of GS lanes per row, one entry per
+// lane, rank = number of smaller (key, position) pairs in the row
+template <int GS>
+__global__ void k_rank_count(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
+                             const int64_t *rows, int64_t nrows, const uint32_t *ekey, RankOut out) {
+    const int lane = threadIdx.x & 31, sub = lane / GS, gl = lane % GS;
+    const unsigned gmask = GS == 32 ? 0xffffffffu : (((1u << GS) - 1u) << (sub * GS));
+    constexpr int RPW = 32 / GS;   // rows per warp
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5) * RPW;
+    for (int64_t t = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + sub; ; t += W) {
+        const bool live = t < nrows;
+        if (!__any_sync(0xffffffffu, live)) break;
+        int64_t i = 0, p0 = 0;
+        int d = 0;
+        if (live) { i = rows[t]; p0 = rp[i]; d = (int)(rp[i + 1] - p0); }
+        const uint32_t k = gl < d ? ekey[p0 + gl] : 0xffffffffu;
+        uint32_t r = 0, lt = 0, leq = 0;
+#pragma unroll
+        for (int l = 0; l < GS; ++l) {
+            const uint32_t o = __shfl_sync(gmask, k, l, GS);
+            if (l < d) {
+                r += (o < k || (o == k && l < gl)) ? 1u : 0u;
+                lt += o < k ? 1u : 0u;
+                leq += o <= k ? 1u : 0u;
+            }
         }
-        if (lane < d) put_rank(info, eid, col, dc, i, p0 + lane, r);
+        if (gl < d) put_ranks(out, eid, col, dc, i, p0 + gl, d, r, lt, leq);
     }
 }
 
-constexpr int kSortCap = 2048;   // entries sorted by one CTA in shared memory
+// rows of degree <= 32 P: one warp sorts the row's (key, position) pairs in
+// registers (bitonic network over index lane * P + j), then writes the ranks
+template <int P>
+__global__ void __launch_bounds__(256) k_rank_wsort(const int64_t *rp, const int32_t *col, const int64_t *eid,
+                                                    const int32_t *dc, const int64_t *rows, int64_t nrows,
+                                                    const uint32_t *ekey, RankOut out) {
+    constexpr int N = 32 * P;
+    const int lane = threadIdx.x & 31;
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < nrows; t += W) {
+        const int64_t i = rows[t];
+        const int64_t p0 = rp[i];
+        const int d = (int)(rp[i + 1] - p0);
+        unsigned long long v[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int idx = lane * P + j;
+            v[j] = idx < d ? (((unsigned long long)ekey[p0 + idx] << 32) | (unsigned)idx) : ~0ull;
+        }
+#pragma unroll
+        for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                if (stride < P) {
+#pragma unroll
+                    for (int j = 0; j < P; ++j) {
+                        if ((j & stride) == 0) {
+                            const int jj = j | stride;
+                            const bool up = (((lane * P + j) & size) == 0);
+                            const unsigned long long a = v[j], b = v[jj];
+                            if ((a > b) == up) { v[j] = b; v[jj] = a; }
+                        }
+                    }
+                } else {
+                    const int ls = stride / P;
+                    const bool lower = (lane & ls) == 0;
+#pragma unroll
+                    for (int j = 0; j < P; ++j) {
+                        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[j], ls);
+                        const bool up = (((lane * P + j) & size) == 0);
+                        v[j] = (lower == up) ? (o < v[j] ? o : v[j]) : (o > v[j] ? o : v[j]);
+                    }
+                }
+            }
+        }
+        // tie runs of equal keys: first = max-scan of run starts, last = min-scan of run ends
+        const uint32_t prev_last = (uint32_t)(__shfl_up_sync(0xffffffffu, v[P - 1], 1) >> 32);
+        const uint32_t next_first = (uint32_t)(__shfl_down_sync(0xffffffffu, v[0], 1) >> 32);
+        int first[P], last[P];
+        int run = 0;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int idx = lane * P + j;
+            const uint32_t kj = (uint32_t)(v[j] >> 32);
+            const uint32_t kp = j > 0 ? (uint32_t)(v[j - 1] >> 32) : prev_last;
+            if (idx == 0 || kj != kp) run = idx;
+            first[j] = run;
+        }
+        int carry = first[P - 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, carry, o);
+            if (lane >= o) carry = max(carry, y);
+        }
+        int excl = __shfl_up_sync(0xffffffffu, carry, 1);
+        if (lane == 0) excl = 0;
+#pragma unroll
+        for (int j = 0; j < P; ++j) first[j] = max(first[j], excl);
+        run = N - 1;
+#pragma unroll
+        for (int j = P - 1; j >= 0; --j) {
+            const int idx = lane * P + j;
+            const uint32_t kj = (uint32_t)(v[j] >> 32);
+            const uint32_t kn = j < P - 1 ? (uint32_t)(v[j + 1] >> 32) : next_first;
+            if (idx == N - 1 || kj != kn) run = idx;
+            last[j] = run;
+        }
+        carry = last[0];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_down_sync(0xffffffffu, carry, o);
+            if (lane + o < 32) carry = min(carry, y);
+        }
+        int excl_r = __shfl_down_sync(0xffffffffu, carry, 1);
+        if (lane == 31) excl_r = N - 1;
+#pragma unroll
+        for (int j = 0; j < P; ++j) last[j] = min(last[j], excl_r);
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+            if (v[j] != ~0ull)
+                put_ranks(out, eid, col, dc, i, p0 + (int64_t)(v[j] & 0xffffffffull), d, (uint32_t)(lane * P + j),
+                          (uint32_t)first[j], (uint32_t)last[j] + 1);
+    }
+}
 
 // Bitonic sort of up to kSortCap 64-bit keys (key << 32 | position) in smem.
 __device__ void block_bitonic(unsigned long long *a, int len_pow2) {
@@ -284,39 +396,40 @@ __device__ void block_bitonic(unsigned long long *a, int len_pow2) {
     }
 }
 
-// rows of degree in (32, kSortCap]: a CTA per row; up to 128 entries rank by
-// counting, longer rows by a bitonic sort of (key, position) in shared memory
+// rows of degree in (128, kSortCap]: a CTA per row, bitonic sort of (key, position)
+__device__ __forceinline__ int lower_bound_smem(const unsigned long long *a, int n, unsigned long long v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 __global__ void k_rank_mid(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
-                           const int32_t *rows, const uint32_t *ekey, int4 *info) {
+                           const int64_t *rows, const uint32_t *ekey, RankOut out) {
     __shared__ unsigned long long a[kSortCap];
     const int64_t row = rows[blockIdx.x];
     const int64_t p0 = rp[row];
     const int d = (int)(rp[row + 1] - p0);
-    if (d <= 128) {
-        for (int t = threadIdx.x; t < d; t += blockDim.x) a[t] = ((unsigned long long)ekey[p0 + t] << 32) | (unsigned)t;
-        __syncthreads();
-        for (int t = threadIdx.x; t < d; t += blockDim.x) {
-            const unsigned long long k = a[t];
-            uint32_t r = 0;
-            for (int u = 0; u < d; ++u) r += a[u] < k ? 1u : 0u;
-            put_rank(info, eid, col, dc, row, p0 + t, r);
-        }
-        return;
-    }
     int len2 = 1;
     while (len2 < d) len2 <<= 1;
     for (int t = threadIdx.x; t < len2; t += blockDim.x)
         a[t] = t < d ? (((unsigned long long)ekey[p0 + t] << 32) | (unsigned)t) : ~0ull;
     __syncthreads();
     block_bitonic(a, len2);
-    for (int t = threadIdx.x; t < d; t += blockDim.x)
-        put_rank(info, eid, col, dc, row, p0 + (int64_t)(a[t] & 0xffffffffull), (uint32_t)t);
+    for (int t = threadIdx.x; t < d; t += blockDim.x) {
+        const unsigned long long k32 = a[t] & 0xffffffff00000000ull;
+        const int lt = lower_bound_smem(a, d, k32);
+        const int leq = lower_bound_smem(a, d, k32 + 0x100000000ull);   // keys of real entries are < 2^32 - 1
+        put_ranks(out, eid, col, dc, row, p0 + (int64_t)(a[t] & 0xffffffffull), d, (uint32_t)t, (uint32_t)lt, (uint32_t)leq);
+    }
 }
 
 // rows of degree > kSortCap: one CTA per (row, chunk of kSortCap entries) sorts
-// the chunk; k_rank_merge then adds the ranks from the other chunks
-__global__ void k_rank_chunks(const int64_t *rp, const int32_t *rows, const int32_t *chunk, const uint32_t *ekey,
-                              uint32_t *rank, unsigned long long *skey) {
+// the chunk into skey (rank inside the chunk into rank)
+__global__ void k_rank_chunks(const int64_t *rp, const int64_t *rows, const int32_t *chunk, const uint32_t *ekey,
+                              uint32_t *rank, uint32_t *lt_arr, uint32_t *leq_arr, unsigned long long *skey) {
     __shared__ unsigned long long a[kSortCap];
     const int64_t row = rows[blockIdx.x];
     const int c = chunk[blockIdx.x];
@@ -331,74 +444,121 @@ __global__ void k_rank_chunks(const int64_t *rp, const int32_t *rows, const int3
     block_bitonic(a, len2);
     for (int t = threadIdx.x; t < len; t += blockDim.x) {
         const int64_t pos = (int64_t)(a[t] & 0xffffffffull);
+        const unsigned long long k32 = a[t] & 0xffffffff00000000ull;
         rank[p0 + pos] = (uint32_t)t;
+        lt_arr[p0 + pos] = (uint32_t)lower_bound_smem(a, len, k32);
+        leq_arr[p0 + pos] = (uint32_t)lower_bound_smem(a, len, k32 + 0x100000000ull);
         skey[p0 + c0 + t] = a[t];
     }
 }
 
-// rows of several chunks: add the number of smaller keys in every other chunk
+// ... then adds, for each entry, the number of smaller keys of every other
+// chunk: each other chunk is staged in shared memory and searched there
 __global__ void k_rank_merge(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
-                             const int32_t *rows, const int32_t *chunk, const uint32_t *ekey,
-                             const unsigned long long *skey, const uint32_t *rank, int4 *info) {
+                             const int64_t *rows, const int32_t *chunk, const uint32_t *ekey,
+                             const unsigned long long *skey, const uint32_t *rank, const uint32_t *lt_arr,
+                             const uint32_t *leq_arr, RankOut out) {
+    __shared__ unsigned long long other[kSortCap];
     const int64_t row = rows[blockIdx.x];
     const int c = chunk[blockIdx.x];
     const int64_t p0 = rp[row], d = rp[row + 1] - p0;
     const int nch = (int)((d + kSortCap - 1) / kSortCap);
     const int64_t c0 = (int64_t)c * kSortCap;
     const int len = (int)std::min<int64_t>(kSortCap, d - c0);
-    for (int t = threadIdx.x; t < len; t += blockDim.x) {
-        const unsigned long long key = ((unsigned long long)ekey[p0 + c0 + t] << 32) | (unsigned long long)(c0 + t);
-        uint32_t add = 0;
-        for (int o = 0; o < nch; ++o) {
-            if (o == c) continue;
-            const int64_t b = p0 + (int64_t)o * kSortCap;
-            int lo = 0, hi = (int)std::min<int64_t>(kSortCap, d - (int64_t)o * kSortCap);
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (skey[b + mid] < key) lo = mid + 1; else hi = mid;
-            }
-            add += (uint32_t)lo;
+    constexpr int kPer = kSortCap / 256;           // entries per thread (blockDim = 256)
+    unsigned long long mine[kPer];
+    uint32_t add[kPer], add_lt[kPer], add_leq[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int t = threadIdx.x + u * 256;
+        mine[u] = t < len ? (((unsigned long long)ekey[p0 + c0 + t] << 32) | (unsigned long long)(c0 + t)) : 0ull;
+        add[u] = 0;
+        add_lt[u] = 0;
+        add_leq[u] = 0;
+    }
+    for (int o = 0; o < nch; ++o) {
+        if (o == c) continue;
+        const int64_t b = p0 + (int64_t)o * kSortCap;
+        const int olen = (int)std::min<int64_t>(kSortCap, d - (int64_t)o * kSortCap);
+        __syncthreads();
+        for (int t = threadIdx.x; t < olen; t += blockDim.x) other[t] = skey[b + t];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const unsigned long long k32 = mine[u] & 0xffffffff00000000ull;
+            add[u] += (uint32_t)lower_bound_smem(other, olen, mine[u]);
+            add_lt[u] += (uint32_t)lower_bound_smem(other, olen, k32);
+            add_leq[u] += (uint32_t)lower_bound_smem(other, olen, k32 + 0x100000000ull);
         }
-        put_rank(info, eid, col, dc, row, p0 + c0 + t, rank[p0 + c0 + t] + add);
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int t = threadIdx.x + u * 256;
+        if (t < len) {
+            const int64_t p = p0 + c0 + t;
+            put_ranks(out, eid, col, dc, row, p, (int)d, rank[p] + add[u], lt_arr[p] + add_lt[u], leq_arr[p] + add_leq[u]);
+        }
     }
 }
 
-// tasks per row: mid rows (32, kSortCap] one, big rows one per chunk
-__global__ void k_chunk_count(const int64_t *rp, int64_t n, int64_t *nmid, int64_t *nbig) {
+// rank class of every row: 0 none, 1 d <= 8, 2 d <= 32, 3 d <= 128, 4 d <= 512, 5 d <= kSortCap, 6 larger
+constexpr int kRankClasses = 7;
+__global__ void k_rank_classes(const int64_t *rp, int64_t n, uint8_t *flags /* [6][n] */) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = rp[i + 1] - rp[i];
-        nmid[i] = (d > 32 && d <= kSortCap) ? 1 : 0;
-        nbig[i] = d > kSortCap ? (d + kSortCap - 1) / kSortCap : 0;
+        const int c = d == 0 ? 0 : d <= 8 ? 1 : d <= 32 ? 2 : d <= 128 ? 3 : d <= 512 ? 4 : d <= kSortCap ? 5 : 6;
+        for (int k = 1; k < kRankClasses; ++k) flags[(int64_t)(k - 1) * n + i] = c == k ? 1 : 0;
     }
 }
-__global__ void k_chunk_expand(const int64_t *nch, const int64_t *first, int64_t n, int32_t *rows, int32_t *chunk) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        for (int64_t c = 0; c < nch[i]; ++c) {
-            rows[first[i] + c] = (int32_t)i;
-            chunk[first[i] + c] = (int32_t)c;
-        }
+
+// First candidate (1..nc) at which the edge is kept, nc + 1 when it is not kept
+// at any; per-graph histograms of that index; the index is stored for compaction.
+__device__ __forceinline__ int graph_of_edge(const int64_t *goff_e, int G, int64_t e) {
+    int lo = 0, hi = G;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(goff_e + mid) <= e) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
-// count the kept set at ncand candidate exponents: T[c][dc] tables per graph
-__global__ void k_count_cand(const int4 *info, const int32_t *tg, const int64_t *ts, const int64_t *te,
-                             const int32_t *T, int32_t ndc, int ncand, unsigned long long *hist) {
-    __shared__ unsigned int h[16];
-    if (threadIdx.x < 16) h[threadIdx.x] = 0;
+__global__ void k_count_cand(const int4 *info, const int64_t *list, int64_t L, const int64_t *goff_e, int G,
+                             const int32_t *T, int32_t ndc, int nc, unsigned long long *hist, uint8_t *cstar) {
+    __shared__ unsigned int h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
     __syncthreads();
-    const int gph = tg[blockIdx.x];
-    const int32_t *Tg = T + (size_t)gph * ncand * ndc;
-    for (int64_t e = ts[blockIdx.x] + threadIdx.x; e < te[blockIdx.x]; e += blockDim.x) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < L; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = list ? list[t] : t;
+        const int gph = G > 1 ? graph_of_edge(goff_e, G, e) : 0;
         const int4 f = info[e];
-        int lo = 0, hi = ncand;   // first candidate at which the edge is kept
+        const int32_t *Tg = T + (size_t)gph * nc * ndc;
+        int lo = 0, hi = nc;   // first candidate index (0-based) at which the edge is kept; nc = none
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             const int32_t *Tm = Tg + (size_t)mid * ndc;
             if (f.x < Tm[f.z] || f.y < Tm[f.w]) hi = mid; else lo = mid + 1;
         }
-        atomicAdd(&h[lo], 1u);
+        cstar[t] = (uint8_t)lo;
+        if (G == 1) atomicAdd(&h[lo], 1u);
+        else atomicAdd(hist + (size_t)gph * 32 + lo, 1ull);
     }
     __syncthreads();
-    if (threadIdx.x < 16 && h[threadIdx.x]) atomicAdd(hist + (size_t)gph * 16 + threadIdx.x, (unsigned long long)h[threadIdx.x]);
+    if (G == 1 && threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(hist + threadIdx.x, (unsigned long long)h[threadIdx.x]);
+}
+
+// undecided edges of the next pass: those whose first candidate is the chosen one
+__global__ void k_undecided_flags(const int64_t *list, int64_t L, const uint8_t *cstar, const int64_t *goff_e, int G,
+                                  const int32_t *jsel, uint8_t *flag) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < L; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = list ? list[t] : t;
+        const int gph = G > 1 ? graph_of_edge(goff_e, G, e) : 0;
+        flag[t] = cstar[t] == jsel[gph] ? 1 : 0;
+    }
+}
+
+__global__ void k_gather_list(const int64_t *list, const int64_t *idx, int64_t L, int64_t *out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < L) out[t] = list ? list[idx[t]] : idx[t];
 }
 
 __global__ void k_keep_at(const int4 *info, const int32_t *tg, const int64_t *ts, const int64_t *te, const int32_t *T,
@@ -423,9 +583,76 @@ __global__ void k_keep_at(const int4 *info, const int32_t *tg, const int64_t *ts
     }
 }
 
+}  // namespace ad
+
 // ----------------------------------------------------------------------------
-// Host side
+// Cached per-graph selection workspace
 // ----------------------------------------------------------------------------
+struct ad_graph_s::SelCache {
+    ad::Tiles tiles;
+    bool have_tiles = false;
+    bool have_lists = false;
+    int64_t *rows[6] = {};          // rows of rank classes 1..6
+    int64_t nrows[6] = {};
+    int64_t *brows = nullptr;       // (row, chunk) tasks of class 6
+    int32_t *bchunk = nullptr;
+    int64_t n_b = 0;
+    ad::DevBuf info, info_desc, ekey, skey, rank, T, hist, list_a, list_b, cstar, flag, jsel, kept, st, hist3, ties,
+        tie_off;
+    bool info_valid = false;      // info / info_desc hold the ranks of the handle's own distances
+    uint64_t info_version = 0;
+};
+
+namespace ad {
+
+void free_sel_cache(ad_graph_t g) {
+    if (!g->sel) return;
+    delete g->sel;   // device memory is owned by the handle and released with it
+    g->sel = nullptr;
+}
+
+static ad_status sel_cache(ad_graph_t g, ad_graph_s::SelCache **out) {
+    if (!g->sel) g->sel = new ad_graph_s::SelCache();
+    auto *c = g->sel;
+    if (!c->have_tiles) {
+        AD_TRY(make_tiles(g, c->tiles));
+        c->have_tiles = true;
+    }
+    *out = c;
+    return AD_OK;
+}
+
+static ad_status rank_lists(ad_graph_t g, ad_graph_s::SelCache *c) {
+    if (c->have_lists) return AD_OK;
+    const int64_t n = g->n;
+    uint8_t *flags = nullptr;
+    AD_TRY(dalloc_t(g, 6 * (n + 1), &flags));
+    if (n > 0) AD_LAUNCH(k_rank_classes, g->num_sms * 8, 256, 0, g->stream, g->rp, n, flags);
+    for (int k = 0; k < 6; ++k) AD_TRY(compact_flags(g, flags + (int64_t)k * n, n, &c->rows[k], &c->nrows[k]));
+    const int64_t nbig = c->nrows[5];
+    if (nbig > 0) {   // few rows: expand (row, chunk) tasks on the host
+        std::vector<int64_t> rows(nbig);
+        AD_TRY(copy_out(g, rows.data(), c->rows[5], nbig * sizeof(int64_t)));
+        std::vector<int64_t> trow;
+        std::vector<int32_t> tch;
+        for (int64_t b = 0; b < nbig; ++b) {
+            int64_t r2[2];
+            AD_TRY(copy_out(g, r2, g->rp + rows[b], 2 * sizeof(int64_t)));
+            const int64_t nch = (r2[1] - r2[0] + kSortCap - 1) / kSortCap;
+            for (int64_t k = 0; k < nch; ++k) { trow.push_back(rows[b]); tch.push_back((int32_t)k); }
+        }
+        c->n_b = (int64_t)trow.size();
+        AD_TRY(dalloc_t(g, c->n_b, &c->brows));
+        AD_TRY(dalloc_t(g, c->n_b, &c->bchunk));
+        AD_TRY(copy_in(g, c->brows, trow.data(), c->n_b * sizeof(int64_t)));
+        AD_TRY(copy_in(g, c->bchunk, tch.data(), c->n_b * sizeof(int32_t)));
+    }
+    dfree(g, flags);
+    c->have_lists = true;
+    return AD_OK;
+}
+
+// T(d, e) of Alg. 2 in FP64 on the host, the reading min(d, max(1, ceil(d^e - 1e-9))).
 int64_t degree_target(int64_t d, double e) {
     if (d <= 0) return 0;
     double t = std::ceil(std::pow((double)d, e) - 1e-9);
@@ -439,8 +666,9 @@ static int64_t target_count(int64_t m, double fraction) { return (int64_t)std::f
 ad_status select_whole_graph(ad_graph_t g, const float *score, double fraction, ad_mode mode, uint8_t *keep,
                              int64_t *n_kept) {
     const int desc = mode == AD_MODE_GLOBAL ? 1 : 0;
-    Tiles t;
-    AD_TRY(make_tiles(g, t));
+    ad_graph_s::SelCache *c = nullptr;
+    AD_TRY(sel_cache(g, &c));
+    const Tiles &t = c->tiles;
     if (t.n == 0) { if (n_kept) *n_kept = 0; return AD_OK; }
     std::vector<SelState> sh(g->G);
     int64_t total = 0;
@@ -453,13 +681,13 @@ ad_status select_whole_graph(ad_graph_t g, const float *score, double fraction, 
         sh[k].k_rem = (sh[k].K > 0 && sh[k].K < m) ? sh[k].K : 0;   // 0: nothing to locate
         total += sh[k].K;
     }
-    SelState *st = nullptr;
-    uint32_t *hist = nullptr;
-    int64_t *ties = nullptr, *tie_off = nullptr;
-    AD_TRY(dalloc_t(g, g->G, &st));
-    AD_TRY(dalloc_t(g, (size_t)g->G * 2048 * 3, &hist));
-    AD_TRY(dalloc_t(g, t.n + 1, &ties));
-    AD_TRY(dalloc_t(g, t.n + 1, &tie_off));
+    AD_TRY(ensure(g, c->st, sizeof(SelState) * g->G));
+    AD_TRY(ensure(g, c->hist3, sizeof(uint32_t) * (size_t)g->G * 2048 * 3));
+    AD_TRY(ensure(g, c->ties, sizeof(int64_t) * (t.n + 1)));
+    AD_TRY(ensure(g, c->tie_off, sizeof(int64_t) * (t.n + 1)));
+    SelState *st = static_cast<SelState *>(c->st.ptr);
+    uint32_t *hist = static_cast<uint32_t *>(c->hist3.ptr);
+    int64_t *ties = static_cast<int64_t *>(c->ties.ptr), *tie_off = static_cast<int64_t *>(c->tie_off.ptr);
     AD_TRY(copy_in(g, st, sh.data(), sizeof(SelState) * g->G));
     AD_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)g->G * 2048 * 3, g->stream));
     const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
@@ -475,72 +703,64 @@ ad_status select_whole_graph(ad_graph_t g, const float *score, double fraction, 
     AD_LAUNCH(k_sel_write, (int)t.n, kTileThreads, 0, g->stream, score, desc, t.graph, t.start, t.end, st, tie_off,
               t.first_tile, keep);
     AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    dfree(g, st);
-    dfree(g, hist);
-    dfree(g, ties);
-    dfree(g, tie_off);
-    free_tiles(g, t);
     if (n_kept) *n_kept = total;
     return AD_OK;
 }
 
-// Ranks of every CSR entry, gathered per edge: the info of Alg. 2.
+// Ranks of every CSR entry in both orders, gathered per edge: the info of
+// Alg. 2.  For the handle's own distances the result is kept until they change.
 static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, int4 **info_out) {
     AD_TRY(ensure_mirror(g));
     AD_TRY(ensure_degree_classes(g));
-    const int desc = mode == AD_MODE_GLOBAL ? 1 : 0;
-    const int64_t n = g->n, nnz = g->nnz;
-    uint32_t *ekey = nullptr, *rank = nullptr;
-    unsigned long long *skey = nullptr;
-    int64_t *nmid = nullptr, *nbig = nullptr, *fmid = nullptr, *fbig = nullptr;
-    int4 *info = nullptr;
-    AD_TRY(dalloc_t(g, g->m + 1, &info));
-    AD_TRY(dalloc_t(g, nnz + 1, &ekey));
-    const int grid = g->num_sms * 16;
-    if (nnz > 0) AD_LAUNCH(k_entry_keys, grid, 256, 0, g->stream, g->eid, nnz, score, desc, ekey);
-    const int64_t wblocks = std::min<int64_t>((n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
-    AD_LAUNCH(k_rank_small, (int)wblocks, 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, n, ekey, info);
-    AD_TRY(dalloc_t(g, n + 1, &nmid));
-    AD_TRY(dalloc_t(g, n + 1, &nbig));
-    AD_TRY(dalloc_t(g, n + 1, &fmid));
-    AD_TRY(dalloc_t(g, n + 1, &fbig));
-    AD_LAUNCH(k_chunk_count, g->num_sms * 8, 256, 0, g->stream, g->rp, n, nmid, nbig);
-    int64_t n_mid = 0, n_big = 0;
-    AD_TRY(exclusive_scan_i64(g, nmid, fmid, n, &n_mid));
-    AD_TRY(exclusive_scan_i64(g, nbig, fbig, n, &n_big));
-    if (n_mid > 0) {
-        int32_t *rows = nullptr, *chunk = nullptr;
-        AD_TRY(dalloc_t(g, n_mid, &rows));
-        AD_TRY(dalloc_t(g, n_mid, &chunk));
-        AD_LAUNCH(k_chunk_expand, g->num_sms * 8, 256, 0, g->stream, nmid, fmid, n, rows, chunk);
-        AD_LAUNCH(k_rank_mid, (int)n_mid, 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows, ekey, info);
-        AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
-        dfree(g, rows);
-        dfree(g, chunk);
+    ad_graph_s::SelCache *c = nullptr;
+    AD_TRY(sel_cache(g, &c));
+    AD_TRY(rank_lists(g, c));
+    const int64_t nnz = g->nnz;
+    AD_TRY(ensure(g, c->info, sizeof(int4) * (g->m + 1)));
+    AD_TRY(ensure(g, c->info_desc, sizeof(int4) * (g->m + 1)));
+    RankOut out;
+    out.asc = static_cast<int4 *>(c->info.ptr);
+    out.desc = static_cast<int4 *>(c->info_desc.ptr);
+    *info_out = mode == AD_MODE_GLOBAL ? out.desc : out.asc;
+    const bool own = score == g->rho && g->have_rho;
+    if (own && c->info_valid && c->info_version == g->rho_version) return AD_OK;
+    c->info_valid = false;
+    AD_TRY(ensure(g, c->ekey, sizeof(uint32_t) * (nnz + 1)));
+    uint32_t *ekey = static_cast<uint32_t *>(c->ekey.ptr);
+    if (nnz > 0) AD_LAUNCH(k_entry_keys, g->num_sms * 16, 256, 0, g->stream, g->eid, nnz, score, 0, ekey);
+    auto wblocks = [&](int64_t rows_, int per_warp) {
+        return (int)std::max<int64_t>(1, std::min<int64_t>((rows_ + 8 * per_warp - 1) / (8 * per_warp),
+                                                           (int64_t)g->num_sms * 32));
+    };
+    if (c->nrows[0] > 0)
+        AD_LAUNCH(k_rank_count<8>, wblocks(c->nrows[0], 4), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class,
+                  c->rows[0], c->nrows[0], ekey, out);
+    if (c->nrows[1] > 0)
+        AD_LAUNCH(k_rank_count<32>, wblocks(c->nrows[1], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class,
+                  c->rows[1], c->nrows[1], ekey, out);
+    if (c->nrows[2] > 0)
+        AD_LAUNCH(k_rank_wsort<4>, wblocks(c->nrows[2], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class,
+                  c->rows[2], c->nrows[2], ekey, out);
+    if (c->nrows[3] > 0)
+        AD_LAUNCH(k_rank_wsort<16>, wblocks(c->nrows[3], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class,
+                  c->rows[3], c->nrows[3], ekey, out);
+    if (c->nrows[4] > 0)
+        AD_LAUNCH(k_rank_mid, (int)c->nrows[4], 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, c->rows[4],
+                  ekey, out);
+    if (c->n_b > 0) {
+        AD_TRY(ensure(g, c->skey, sizeof(unsigned long long) * (nnz + 1)));
+        AD_TRY(ensure(g, c->rank, sizeof(uint32_t) * 3 * (nnz + 1)));
+        unsigned long long *skey = static_cast<unsigned long long *>(c->skey.ptr);
+        uint32_t *rank = static_cast<uint32_t *>(c->rank.ptr);
+        uint32_t *lt = rank + (nnz + 1), *leq = rank + 2 * (nnz + 1);
+        AD_LAUNCH(k_rank_chunks, (int)c->n_b, 512, 0, g->stream, g->rp, c->brows, c->bchunk, ekey, rank, lt, leq, skey);
+        AD_LAUNCH(k_rank_merge, (int)c->n_b, 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, c->brows,
+                  c->bchunk, ekey, skey, rank, lt, leq, out);
     }
-    if (n_big > 0) {
-        int32_t *rows = nullptr, *chunk = nullptr;
-        AD_TRY(dalloc_t(g, n_big, &rows));
-        AD_TRY(dalloc_t(g, n_big, &chunk));
-        AD_TRY(dalloc_t(g, nnz + 1, &skey));
-        AD_TRY(dalloc_t(g, nnz + 1, &rank));
-        AD_LAUNCH(k_chunk_expand, g->num_sms * 8, 256, 0, g->stream, nbig, fbig, n, rows, chunk);
-        AD_LAUNCH(k_rank_chunks, (int)n_big, 512, 0, g->stream, g->rp, rows, chunk, ekey, rank, skey);
-        AD_LAUNCH(k_rank_merge, (int)n_big, 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows, chunk, ekey,
-                  skey, rank, info);
-        AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
-        dfree(g, rows);
-        dfree(g, chunk);
-        dfree(g, skey);
-        dfree(g, rank);
+    if (own) {
+        c->info_valid = true;
+        c->info_version = g->rho_version;
     }
-    AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    dfree(g, ekey);
-    dfree(g, nmid);
-    dfree(g, nbig);
-    dfree(g, fmid);
-    dfree(g, fbig);
-    *info_out = info;
     return AD_OK;
 }
 
@@ -548,15 +768,17 @@ static void fill_table(const std::vector<int64_t> &deg, double e, int32_t *out) 
     for (size_t c = 0; c < deg.size(); ++c) out[c] = (int32_t)degree_target(deg[c], e);
 }
 
-static ad_status keep_at(ad_graph_t g, const int4 *info, const Tiles &t, const std::vector<double> &e_per_graph,
-                         uint8_t *keep, int64_t *n_kept) {
+static ad_status keep_at(ad_graph_t g, const int4 *info, const std::vector<double> &e_per_graph, uint8_t *keep,
+                         int64_t *n_kept) {
+    ad_graph_s::SelCache *c = g->sel;
+    const Tiles &t = c->tiles;
     const int32_t ndc = std::max<int32_t>(g->n_deg_classes, 1);
     std::vector<int32_t> Th((size_t)g->G * ndc, 0);
     for (int32_t k = 0; k < g->G; ++k) fill_table(g->distinct_degrees, e_per_graph[k], Th.data() + (size_t)k * ndc);
-    int32_t *T = nullptr;
-    unsigned long long *kept = nullptr;
-    AD_TRY(dalloc_t(g, Th.size(), &T));
-    AD_TRY(dalloc_t(g, g->G, &kept));
+    AD_TRY(ensure(g, c->T, Th.size() * sizeof(int32_t)));
+    AD_TRY(ensure(g, c->kept, sizeof(unsigned long long) * g->G));
+    int32_t *T = static_cast<int32_t *>(c->T.ptr);
+    unsigned long long *kept = static_cast<unsigned long long *>(c->kept.ptr);
     AD_TRY(copy_in(g, T, Th.data(), Th.size() * sizeof(int32_t)));
     AD_CUDA_TRY(cudaMemsetAsync(kept, 0, sizeof(unsigned long long) * g->G, g->stream));
     if (t.n > 0)
@@ -566,8 +788,6 @@ static ad_status keep_at(ad_graph_t g, const int4 *info, const Tiles &t, const s
     int64_t tot = 0;
     for (auto v : kh) tot += (int64_t)v;
     if (n_kept) *n_kept = tot;
-    dfree(g, T);
-    dfree(g, kept);
     return AD_OK;
 }
 
@@ -575,79 +795,125 @@ ad_status select_per_node_at(ad_graph_t g, const float *score, double e, ad_mode
                              int64_t *n_kept) {
     int4 *info = nullptr;
     AD_TRY(per_node_info(g, score, mode, &info));
-    Tiles t;
-    AD_TRY(make_tiles(g, t));
     std::vector<double> ev(g->G, e);
-    ad_status st = keep_at(g, info, t, ev, keep, n_kept);
-    free_tiles(g, t);
-    dfree(g, info);
-    return st;
+    return keep_at(g, info, ev, keep, n_kept);
 }
 
 // Smallest grid point j * 2^-40 (0 < j <= 2^40) whose kept count reaches K,
-// per graph, searched with 15 candidates per pass (the same result as 40
-// halvings of [0, 1] because the kept count is monotone in e).
+// per graph (the result of 40 halvings of [0, 1], because the kept count is
+// monotone in e).  Each pass counts the kept set at 15 interior points of the
+// current interval and its upper end; edges whose fate the chosen
+// sub-interval already decides drop out of the next pass.
 ad_status select_per_node_fit(ad_graph_t g, const float *score, double fraction, ad_mode mode, uint8_t *keep,
                               int64_t *n_kept, double *e_used) {
     int4 *info = nullptr;
     AD_TRY(per_node_info(g, score, mode, &info));
-    Tiles t;
-    AD_TRY(make_tiles(g, t));
+    ad_graph_s::SelCache *c = g->sel;
     const int32_t ndc = std::max<int32_t>(g->n_deg_classes, 1);
-    const int ncand = 15;
+    const int ncand = 16;   // 15 interior points + the upper end
     const int64_t ONE = (int64_t)1 << 40;
-    std::vector<int64_t> lo(g->G, 0), hi(g->G, ONE), K(g->G);
-    for (int32_t k = 0; k < g->G; ++k) K[k] = target_count(g->eoff_h[k + 1] - g->eoff_h[k], fraction);
-    int32_t *T = nullptr;
-    unsigned long long *hist = nullptr;
-    AD_TRY(dalloc_t(g, (size_t)g->G * ncand * ndc, &T));
-    AD_TRY(dalloc_t(g, (size_t)g->G * 16, &hist));
-    std::vector<int32_t> Th((size_t)g->G * ncand * ndc);
-    std::vector<unsigned long long> hh((size_t)g->G * 16);
-    std::vector<std::vector<int64_t>> cand(g->G);
+    const int G = g->G;
+    std::vector<int64_t> lo(G, 0), hi(G, ONE), K(G), base(G, 0);
+    for (int32_t k = 0; k < G; ++k) K[k] = target_count(g->eoff_h[k + 1] - g->eoff_h[k], fraction);
+    AD_TRY(ensure(g, c->T, (size_t)G * ncand * ndc * sizeof(int32_t)));
+    AD_TRY(ensure(g, c->hist, (size_t)G * 32 * sizeof(unsigned long long)));
+    AD_TRY(ensure(g, c->jsel, (size_t)(G + 1) * sizeof(int32_t)));
+    AD_TRY(ensure(g, c->cstar, (size_t)(g->m + 1)));
+    AD_TRY(ensure(g, c->flag, (size_t)(g->m + 1)));
+    int32_t *T = static_cast<int32_t *>(c->T.ptr);
+    unsigned long long *hist = static_cast<unsigned long long *>(c->hist.ptr);
+    int32_t *jsel_d = static_cast<int32_t *>(c->jsel.ptr);
+    uint8_t *cstar = static_cast<uint8_t *>(c->cstar.ptr), *flag = static_cast<uint8_t *>(c->flag.ptr);
+    std::vector<int32_t> Th((size_t)G * ncand * ndc);
+    std::vector<unsigned long long> hh((size_t)G * 32);
+    std::vector<std::vector<int64_t>> cand(G);
+    std::vector<int32_t> jsel(G + 1, -1);
+    // T at the current interval ends (e = 0: every node keeps 1; e = 1: all of its edges).
+    // T is monotone in e, so a class with equal values at both ends is constant inside.
+    std::vector<int32_t> Tlo((size_t)G * ndc, 1), Thi((size_t)G * ndc, 0);
+    for (int32_t k = 0; k < G; ++k)
+        for (int32_t q = 0; q < g->n_deg_classes; ++q) Thi[(size_t)k * ndc + q] = (int32_t)g->distinct_degrees[q];
+    const int64_t *list = nullptr;   // nullptr: all edges
+    int64_t L = g->m;
+    int64_t *owned_list = nullptr;
     for (;;) {
         bool any = false;
-        for (int32_t k = 0; k < g->G; ++k) {
+        for (int32_t k = 0; k < G; ++k) {
             cand[k].clear();
             const int64_t span = hi[k] - lo[k];
             if (span > 1) {
                 any = true;
                 const int64_t step = (span + 15) / 16;
-                for (int64_t j = lo[k] + step; j < hi[k] && (int)cand[k].size() < ncand; j += step) cand[k].push_back(j);
+                for (int64_t j = lo[k] + step; j < hi[k] && (int)cand[k].size() < ncand - 1; j += step) cand[k].push_back(j);
             }
-            for (int c = 0; c < ncand; ++c) {
-                // unused slots repeat hi (kept count there is >= K already)
-                const int64_t j = c < (int)cand[k].size() ? cand[k][c] : hi[k];
-                fill_table(g->distinct_degrees, std::ldexp((double)j, -40), Th.data() + ((size_t)k * ncand + c) * ndc);
+            cand[k].push_back(hi[k]);
+            const int32_t *tl = Tlo.data() + (size_t)k * ndc, *th = Thi.data() + (size_t)k * ndc;
+            for (int cc = 0; cc < ncand; ++cc) {
+                const int64_t j = cc < (int)cand[k].size() ? cand[k][cc] : hi[k];
+                int32_t *out = Th.data() + ((size_t)k * ncand + cc) * ndc;
+                if (j == hi[k]) {
+                    for (int32_t q = 0; q < ndc; ++q) out[q] = th[q];
+                    continue;
+                }
+                const double e = std::ldexp((double)j, -40);
+                for (int32_t q = 0; q < g->n_deg_classes; ++q)
+                    out[q] = tl[q] == th[q] ? tl[q] : (int32_t)degree_target(g->distinct_degrees[q], e);
             }
         }
-        if (!any) break;
+        if (!any || L == 0) break;
         AD_TRY(copy_in(g, T, Th.data(), Th.size() * sizeof(int32_t)));
-        AD_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * g->G * 16, g->stream));
-        if (t.n > 0)
-            AD_LAUNCH(k_count_cand, (int)t.n, 256, 0, g->stream, info, t.graph, t.start, t.end, T, ndc, ncand, hist);
+        AD_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * G * 32, g->stream));
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((L + 255) / 256, (int64_t)g->num_sms * 16));
+        AD_LAUNCH(k_count_cand, blocks, 256, 0, g->stream, info, list, L, g->goff_e, G, T, ndc, ncand, hist, cstar);
         AD_TRY(copy_out(g, hh.data(), hist, sizeof(unsigned long long) * hh.size()));
-        for (int32_t k = 0; k < g->G; ++k) {
-            int64_t cum = 0;
-            int64_t new_lo = lo[k], new_hi = hi[k];
-            for (int c = 0; c < (int)cand[k].size(); ++c) {
-                cum += (int64_t)hh[(size_t)k * 16 + c];
-                if (cum >= K[k]) { new_hi = cand[k][c]; break; }
-                new_lo = cand[k][c];
+        for (int32_t k = 0; k < G; ++k) {
+            if (hi[k] - lo[k] <= 1) { jsel[k] = -1; continue; }
+            int64_t cum = base[k];
+            int chosen = (int)cand[k].size() - 1;   // the upper end always reaches K
+            for (int cc = 0; cc < (int)cand[k].size(); ++cc) {
+                cum += (int64_t)hh[(size_t)k * 32 + cc];
+                if (cum >= K[k]) { chosen = cc; break; }
             }
-            lo[k] = new_lo;
-            hi[k] = new_hi;
+            // edges first kept before the chosen point stay kept in the new interval
+            for (int cc = 0; cc < chosen; ++cc) base[k] += (int64_t)hh[(size_t)k * 32 + cc];
+            if (chosen > 0) {
+                const int32_t *src = Th.data() + ((size_t)k * ncand + chosen - 1) * ndc;
+                std::copy(src, src + ndc, Tlo.begin() + (size_t)k * ndc);
+            }
+            {
+                const int32_t *src = Th.data() + ((size_t)k * ncand + chosen) * ndc;
+                std::copy(src, src + ndc, Thi.begin() + (size_t)k * ndc);
+            }
+            lo[k] = chosen > 0 ? cand[k][chosen - 1] : lo[k];
+            hi[k] = cand[k][chosen];
+            jsel[k] = chosen;
         }
+        // next pass: the edges whose first kept point is the chosen one
+        AD_TRY(copy_in(g, jsel_d, jsel.data(), (G + 1) * sizeof(int32_t)));
+        const int fblocks = (int)std::max<int64_t>(1, std::min<int64_t>((L + 255) / 256, (int64_t)g->num_sms * 16));
+        AD_LAUNCH(k_undecided_flags, fblocks, 256, 0, g->stream, list, L, cstar, g->goff_e, G, jsel_d, flag);
+        int64_t *idx = nullptr, nL = 0;
+        AD_TRY(compact_flags(g, flag, L, &idx, &nL));
+        int64_t *next = nullptr;
+        if (nL > 0) {
+            AD_TRY(dalloc_t(g, nL, &next));
+            AD_LAUNCH(k_gather_list, (int)((nL + 255) / 256), 256, 0, g->stream, list, idx, nL, next);
+        }
+        if (idx) dfree(g, idx);
+        if (owned_list) dfree(g, owned_list);
+        owned_list = next;
+        list = next;
+        L = nL;
     }
-    std::vector<double> ev(g->G);
-    for (int32_t k = 0; k < g->G; ++k) ev[k] = std::ldexp((double)hi[k], -40);
-    ad_status st = keep_at(g, info, t, ev, keep, n_kept);
-    if (e_used) *e_used = g->G > 0 ? ev[0] : -1.0;
-    dfree(g, T);
-    dfree(g, hist);
-    free_tiles(g, t);
-    dfree(g, info);
-    return st;
+    if (owned_list) dfree(g, owned_list);
+    // no undecided edge left: the count is constant on (lo, hi], so the first grid point reaches K
+    for (int32_t k = 0; k < G; ++k)
+        if (hi[k] - lo[k] > 1) hi[k] = lo[k] + 1;
+    std::vector<double> ev(G);
+    for (int32_t k = 0; k < G; ++k) ev[k] = std::ldexp((double)hi[k], -40);
+    AD_TRY(keep_at(g, info, ev, keep, n_kept));
+    if (e_used) *e_used = G > 0 ? ev[0] : -1.0;
+    return AD_OK;
 }
 
 ad_status check_scores(ad_graph_t g, const float *score) {

@@ -169,3 +169,33 @@ def test_full_size_rmat20_selection_bit_exact():
     kept, _ = L.ad_sparsify_scores(h, s, 0.3, "local", "whole_graph", keep)
     np.testing.assert_array_equal(keep, oracle.select_whole_graph(s.astype(np.float64), "local", kept))
     L.ad_graph_destroy(h)
+
+
+def test_cached_ranks_follow_the_distances():
+    """Ranks of the handle's own distances are kept between calls; they must
+    be rebuilt after the distances change and never be reused for user
+    scores (Alg. 2 on whatever scores the call names)."""
+    L = lib()
+    g = graphgen.rmat(13, 16, seed=8)
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
+    rho = np.zeros(g.m, np.float32)
+    keep = np.zeros(g.m, np.uint8)
+
+    def check_own(mode):
+        kept, e = L.ad_sparsify(h, 0.3, mode, "per_node", keep)
+        ref, rk, re_ = oracle.sparsify(g.row_ptr, g.col, rho.astype(np.float64), mode, "per_node", 0.3)
+        assert e == re_ and kept == rk
+        np.testing.assert_array_equal(keep, ref)
+
+    L.ad_algebraic_distance(h, 16, 10, 0.5, 1, 0, "fp32", 0, rho)
+    for mode in ("local", "global", "local"):
+        check_own(mode)
+    s = graphgen.random_scores(g.m, 25, seed=9)
+    kept, e = L.ad_sparsify_scores(h, s, 0.3, "global", "per_node", keep)
+    np.testing.assert_array_equal(keep, oracle.sparsify(g.row_ptr, g.col, s.astype(np.float64), "global",
+                                                        "per_node", 0.3)[0])
+    check_own("global")
+    L.ad_algebraic_distance(h, 16, 10, 0.5, 2, 0, "fp32", 0, rho)     # new seed: new distances
+    check_own("global")
+    check_own("local")
+    L.ad_graph_destroy(h)
