@@ -235,6 +235,27 @@ def ws_batch(G: int = 512, n_lo=1000, n_hi=200000, k=10, p=0.1, seed: int = 8):
     return [watts_strogatz(int(s), k, p, seed=seed * 100003 + i) for i, s in enumerate(sizes)]
 
 
+def concat(graphs) -> tuple[np.ndarray, Graph]:
+    """Disjoint union of graphs as one block-diagonal CSR (graph g owns
+    vertices voff[g]..voff[g+1]-1), built by offsetting the CSR arrays.
+    Returns (voff int64[G+1], union)."""
+    voff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    voff[1:] = np.cumsum([gg.n for gg in graphs])
+    eoff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    eoff[1:] = np.cumsum([gg.nnz for gg in graphs])
+    row_ptr = np.empty(int(voff[-1]) + 1, dtype=np.int64)
+    col = np.empty(int(eoff[-1]), dtype=np.int32)
+    weighted = any(gg.weight is not None for gg in graphs)
+    weight = np.empty(int(eoff[-1]), dtype=np.float32) if weighted else None
+    for gg, v0, e0 in zip(graphs, voff, eoff):
+        row_ptr[v0:v0 + gg.n] = gg.row_ptr[:-1] + e0
+        col[e0:e0 + gg.nnz] = gg.col + np.int32(v0)
+        if weighted:
+            weight[e0:e0 + gg.nnz] = 1.0 if gg.weight is None else gg.weight
+    row_ptr[-1] = eoff[-1]
+    return voff, Graph(n=int(voff[-1]), row_ptr=row_ptr, col=col, weight=weight, name="union")
+
+
 def random_scores(m: int, n_distinct: int | None = None, seed: int = 9) -> np.ndarray:
     """Non-negative FP32 edge scores for selection tests; with n_distinct the
     values repeat so that ties occur."""
