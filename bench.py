@@ -10,8 +10,10 @@ resident in device memory when the timed region starts.
 Metric: edge-vector updates per second = nnz * R * k / step time (nnz counts
 both CSR directions).  Also reported: the end-to-end figure through the C ABI
 with host buffers (graph upload and result download inside the timed region),
-the HBM roofline fraction of the dominant kernel (one JOR sweep), and the FP64
-oracle timed on the host cores on a bounded sample of the same workload.
+the HBM roofline fraction of the dominant kernel (one JOR sweep), the same step
+with BF16 and FP16 storage of the test vectors (FP32 accumulation) and their
+accuracy against the FP32 path, and the FP64 oracle timed on the host cores on
+a bounded sample of the same workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|bf16|fp16|q16]
     python bench.py --impl reference      # the FP64 CPU oracle, same metric
@@ -245,6 +247,45 @@ def run_gpu(args):
     units = g.nnz * R * K_SWEEPS
     value = ws * args.steps * units / (ms / 1e3)
 
+    # the same step with 16-bit storage of the test vectors (FP32 accumulation), and its
+    # accuracy against the FP32 path (itself within 1e-5 of the FP64 oracle)
+    variants = {}
+    if args.variants:
+        rho32 = torch.empty(g.m, dtype=torch.float32, device=dev)
+        L.ad_algebraic_distance(h, R, K_SWEEPS, OMEGA, SEED, 0, storage, 0, rho32)
+        L.ad_sparsify(h, FRACTION, "local", "per_node", keep_d)
+        keep32 = keep_d.clone()
+        for st in ("bf16", "fp16"):
+            if st == storage:
+                continue
+
+            def vstep(handle, keep, st=st):
+                L.ad_algebraic_distance(handle, R, K_SWEEPS, OMEGA, SEED, 0, st, 0, None)
+                L.ad_sparsify(handle, FRACTION, "local", "per_node", keep)
+                L.ad_sparsify(handle, FRACTION, "global", "per_node", keep)
+            for _ in range(args.warmup):
+                vstep(h, keep_d)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                vstep(h, keep_d)
+            e1.record(stream)
+            barrier()
+            vms = max_over_ranks(e0.elapsed_time(e1))
+            rv = torch.empty(g.m, dtype=torch.float32, device=dev)
+            L.ad_algebraic_distance(h, R, K_SWEEPS, OMEGA, SEED, 0, st, 0, rv)
+            L.ad_sparsify(h, FRACTION, "local", "per_node", keep_d)
+            d = (rv.double() - rho32.double())
+            inter = int((keep_d.bool() & keep32.bool()).sum())
+            union = int((keep_d.bool() | keep32.bool()).sum())
+            variants[st] = {"value": ws * args.steps * g.nnz * R * K_SWEEPS / (vms / 1e3), "unit": UNIT,
+                            "ms_per_step": vms / args.steps,
+                            "rho_rms_rel_err_vs_fp32": float(d.pow(2).mean().sqrt() / rho32.double().pow(2).mean().sqrt()),
+                            "rho_max_err_over_rms_vs_fp32": float(d.abs().max() / rho32.double().pow(2).mean().sqrt()),
+                            "jaccard_local_30pct_vs_fp32": inter / max(union, 1)}
+        del rho32, keep32
+
     # phase split and the dominant kernel's launch time (events on the handle's stream)
     L.ad_graph_set_profiling(h, True)
     for ph in ("init", "sweep", "distance", "select"):
@@ -301,6 +342,7 @@ def run_gpu(args):
                              "peak_kind": peak_kind, "algorithmic_bytes_per_launch": b_sweep,
                              "avg_launch_ms": sweep_ms, "traffic": sweep_traffic(storage)},
                 "gpu_launches": int(launches),
+                "storage_variants": variants or None,
                 "clocks": clk}
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g)
@@ -320,6 +362,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16", "q16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the 16-bit storage comparison")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT scale; values other than 20 are smaller profiling cases, not the benchmark")
     args = ap.parse_args()

@@ -397,8 +397,8 @@ __global__ void k_bw_ybar(const float *xbar, const int64_t *rp, const float *Din
 __global__ void k_scale_from_mm(const uint32_t *mn, const uint32_t *mx, int32_t stride, float *a) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= stride) return;
-    const double lo = ord2f(mn[r]), hi = ord2f(mx[r]);
-    a[r] = hi > lo ? (float)(1.0 / (hi - lo)) : 0.f;
+    const float lo = ord2f(mn[r]), hi = ord2f(mx[r]);   // the forward sweeps' scale, bit for bit
+    a[r] = hi > lo ? 1.f / (hi - lo) : 0.f;
 }
 
 // dL/dw_e from the per-entry and per-row accumulators of both directions of e

@@ -426,87 +426,74 @@ __global__ void k_rank_mid(const int64_t *rp, const int32_t *col, const int64_t 
     }
 }
 
-// rows of degree > kSortCap: one CTA per (row, chunk of kSortCap entries) sorts
-// the chunk into skey (rank inside the chunk into rank)
-__global__ void k_rank_chunks(const int64_t *rp, const int64_t *rows, const int32_t *chunk, const uint32_t *ekey,
-                              uint32_t *rank, uint32_t *lt_arr, uint32_t *leq_arr, unsigned long long *skey) {
-    __shared__ unsigned long long a[kSortCap];
+// Rows of degree > kSortCap.  Their entries are listed once per handle
+// (position bpos and row slot bseg, row slots in bstart order); each call sorts
+// (row slot, key) with the stable radix sort, whose input order is by position
+// inside a row, so each row's entries end up in (key, position) order.
+__global__ void k_big_expand(const int64_t *rows, const int64_t *rp, const int64_t *bstart, int64_t *bpos,
+                             int32_t *bseg) {
     const int64_t row = rows[blockIdx.x];
-    const int c = chunk[blockIdx.x];
-    const int64_t p0 = rp[row], d = rp[row + 1] - p0;
-    const int64_t c0 = (int64_t)c * kSortCap;
-    const int len = (int)std::min<int64_t>(kSortCap, d - c0);
-    int len2 = 1;
-    while (len2 < len) len2 <<= 1;
-    for (int t = threadIdx.x; t < len2; t += blockDim.x)
-        a[t] = t < len ? (((unsigned long long)ekey[p0 + c0 + t] << 32) | (unsigned long long)(c0 + t)) : ~0ull;
-    __syncthreads();
-    block_bitonic(a, len2);
-    for (int t = threadIdx.x; t < len; t += blockDim.x) {
-        const int64_t pos = (int64_t)(a[t] & 0xffffffffull);
-        const unsigned long long k32 = a[t] & 0xffffffff00000000ull;
-        rank[p0 + pos] = (uint32_t)t;
-        lt_arr[p0 + pos] = (uint32_t)lower_bound_smem(a, len, k32);
-        leq_arr[p0 + pos] = (uint32_t)lower_bound_smem(a, len, k32 + 0x100000000ull);
-        skey[p0 + c0 + t] = a[t];
+    const int64_t p0 = rp[row], d = rp[row + 1] - p0, o = bstart[blockIdx.x];
+    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
+        bpos[o + t] = p0 + t;
+        bseg[o + t] = (int32_t)blockIdx.x;
     }
 }
 
-// ... then adds, for each entry, the number of smaller keys of every other
-// chunk: each other chunk is staged in shared memory and searched there
-__global__ void k_rank_merge(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
-                             const int64_t *rows, const int32_t *chunk, const uint32_t *ekey,
-                             const unsigned long long *skey, const uint32_t *rank, const uint32_t *lt_arr,
-                             const uint32_t *leq_arr, RankOut out) {
-    __shared__ unsigned long long other[kSortCap];
-    const int64_t row = rows[blockIdx.x];
-    const int c = chunk[blockIdx.x];
-    const int64_t p0 = rp[row], d = rp[row + 1] - p0;
-    const int nch = (int)((d + kSortCap - 1) / kSortCap);
-    const int64_t c0 = (int64_t)c * kSortCap;
-    const int len = (int)std::min<int64_t>(kSortCap, d - c0);
-    constexpr int kPer = kSortCap / 256;           // entries per thread (blockDim = 256)
-    unsigned long long mine[kPer];
-    uint32_t add[kPer], add_lt[kPer], add_leq[kPer];
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        const int t = threadIdx.x + u * 256;
-        mine[u] = t < len ? (((unsigned long long)ekey[p0 + c0 + t] << 32) | (unsigned long long)(c0 + t)) : 0ull;
-        add[u] = 0;
-        add_lt[u] = 0;
-        add_leq[u] = 0;
-    }
-    for (int o = 0; o < nch; ++o) {
-        if (o == c) continue;
-        const int64_t b = p0 + (int64_t)o * kSortCap;
-        const int olen = (int)std::min<int64_t>(kSortCap, d - (int64_t)o * kSortCap);
-        __syncthreads();
-        for (int t = threadIdx.x; t < olen; t += blockDim.x) other[t] = skey[b + t];
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const unsigned long long k32 = mine[u] & 0xffffffff00000000ull;
-            add[u] += (uint32_t)lower_bound_smem(other, olen, mine[u]);
-            add_lt[u] += (uint32_t)lower_bound_smem(other, olen, k32);
-            add_leq[u] += (uint32_t)lower_bound_smem(other, olen, k32 + 0x100000000ull);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        const int t = threadIdx.x + u * 256;
-        if (t < len) {
-            const int64_t p = p0 + c0 + t;
-            put_ranks(out, eid, col, dc, row, p, (int)d, rank[p] + add[u], lt_arr[p] + add_lt[u], leq_arr[p] + add_leq[u]);
-        }
+__global__ void k_big_keys(const int64_t *bpos, const int32_t *bseg, int64_t nb, const uint32_t *ekey,
+                           uint64_t *keys, int64_t *vals) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = bpos[i];
+        keys[i] = ((uint64_t)(uint32_t)bseg[i] << 32) | ekey[p];
+        vals[i] = p;
     }
 }
 
-// rank class of every row: 0 none, 1 d <= 8, 2 d <= 32, 3 d <= 128, 4 d <= 512, 5 d <= kSortCap, 6 larger
-constexpr int kRankClasses = 7;
-__global__ void k_rank_classes(const int64_t *rp, int64_t n, uint8_t *flags /* [6][n] */) {
+// after the sort: rank = index inside the row's run of the sorted array; the
+// first and last index of a run of equal keys give lt and leq (binary search
+// only where a neighbour holds the same key)
+__global__ void k_big_ranks(const uint64_t *keys, const int64_t *vals, int64_t nb, const int64_t *bstart,
+                            const int64_t *rows, const int64_t *eid, const int32_t *col, const int32_t *dc,
+                            RankOut out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nb; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[t];
+        const int b = (int)(k >> 32);
+        const int64_t s = bstart[b], e = bstart[b + 1];
+        int64_t lt = t, le = t + 1;
+        if (t > s && keys[t - 1] == k) {
+            int64_t lo = s, hi = t;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (keys[mid] < k) lo = mid + 1; else hi = mid;
+            }
+            lt = lo;
+        }
+        if (t + 1 < e && keys[t + 1] == k) {
+            int64_t lo = t + 1, hi = e;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (keys[mid] <= k) lo = mid + 1; else hi = mid;
+            }
+            le = lo;
+        }
+        put_ranks(out, eid, col, dc, rows[b], vals[t], (int)(e - s), (uint32_t)(t - s), (uint32_t)(lt - s),
+                  (uint32_t)(le - s));
+    }
+}
+
+__global__ void k_row_degrees(const int64_t *rows, int64_t nrows, const int64_t *rp, int64_t *deg) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < nrows) deg[i] = rp[rows[i] + 1] - rp[rows[i]];
+}
+
+// rank class of every row: 0 none, 1 d <= 8, 2 d <= 32, 3 d <= 64, 4 d <= 128, 5 d <= 256, 6 d <= 512,
+// 7 d <= kSortCap, 8 larger
+constexpr int kRankClasses = 9;
+__global__ void k_rank_classes(const int64_t *rp, int64_t n, uint8_t *flags /* [kRankClasses - 1][n] */) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = rp[i + 1] - rp[i];
-        const int c = d == 0 ? 0 : d <= 8 ? 1 : d <= 32 ? 2 : d <= 128 ? 3 : d <= 512 ? 4 : d <= kSortCap ? 5 : 6;
+        const int c = d == 0 ? 0 : d <= 8 ? 1 : d <= 32 ? 2 : d <= 64 ? 3 : d <= 128 ? 4 : d <= 256 ? 5 : d <= 512 ? 6
+                    : d <= kSortCap ? 7 : 8;
         for (int k = 1; k < kRankClasses; ++k) flags[(int64_t)(k - 1) * n + i] = c == k ? 1 : 0;
     }
 }
@@ -522,11 +509,12 @@ __device__ __forceinline__ int graph_of_edge(const int64_t *goff_e, int G, int64
     return lo;
 }
 
-__global__ void k_count_cand(const int4 *info, const int64_t *list, int64_t L, const int64_t *goff_e, int G,
-                             const int32_t *T, int32_t ndc, int nc, unsigned long long *hist, uint8_t *cstar) {
+__global__ void k_count_cand(const int4 *info, const int64_t *list, int64_t L, const int64_t *Ld, const int64_t *goff_e,
+                             int G, const int32_t *T, int32_t ndc, int nc, unsigned long long *hist, uint8_t *cstar) {
     __shared__ unsigned int h[32];
     if (threadIdx.x < 32) h[threadIdx.x] = 0;
     __syncthreads();
+    if (Ld) L = *Ld;    // length of a list compacted on the device
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < L; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = list ? list[t] : t;
         const int gph = G > 1 ? graph_of_edge(goff_e, G, e) : 0;
@@ -561,6 +549,102 @@ __global__ void k_gather_list(const int64_t *list, const int64_t *idx, int64_t L
     if (t < L) out[t] = list ? list[idx[t]] : idx[t];
 }
 
+// ----------------------------------------------------------------------------
+// Device-resident search of the exponent (same passes as the host loop of
+// select_per_node_fit_host, without a host round trip per pass).  T(d, e) is
+// evaluated with the device pow; where d^e - 1e-9 lies so close to an integer
+// that a pow differing from the host's by a few units in the last place could
+// round the other way, the pass raises a flag and the caller repeats the
+// search with host tables, so the integer decisions stay those of FP64 pow on
+// the host.
+// ----------------------------------------------------------------------------
+struct FitState {
+    int64_t lo, hi, K, base;
+    int32_t jsel, pad;
+};
+
+constexpr int kFitCand = 16;          // 15 interior grid points + the upper end
+constexpr int kFitPasses = 10;        // 16^10 = 2^40: every interval shrinks to one grid step
+
+__device__ __forceinline__ int fit_interior(const FitState &s, int64_t &step) {
+    const int64_t span = s.hi - s.lo;
+    if (span <= 1) { step = 0; return 0; }
+    step = (span + kFitCand - 1) / kFitCand;
+    const int64_t n = (span - 1) / step;
+    return (int)(n < kFitCand - 1 ? n : kFitCand - 1);
+}
+
+__device__ __forceinline__ int64_t fit_point(const FitState &s, int cc) {
+    int64_t step;
+    const int ni = fit_interior(s, step);
+    return cc < ni ? s.lo + step * (cc + 1) : s.hi;
+}
+
+__global__ void k_fit_tables(const FitState *st, int G, const int64_t *ddeg, int32_t ndc, int32_t *T, int *ambiguous) {
+    const int64_t total = (int64_t)G * kFitCand * ndc;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(idx % ndc);
+        const int64_t kc = idx / ndc;
+        const int cc = (int)(kc % kFitCand), k = (int)(kc / kFitCand);
+        const int64_t d = ddeg[q];
+        int32_t t = 0;
+        if (d > 0) {
+            const double e = ldexp((double)fit_point(st[k], cc), -40);
+            const double v = pow((double)d, e);
+            const double x = v - 1e-9;
+            const double f = x - floor(x);
+            const double tol = 4e-15 * fmax(v, 1.0);
+            if (f < tol || f > 1.0 - tol) atomicExch(ambiguous, 1);
+            double c = ceil(x);
+            if (c < 1.0) c = 1.0;
+            if (c > (double)d) c = (double)d;
+            t = (int32_t)c;
+        }
+        T[idx] = t;
+    }
+}
+
+// per graph: the first candidate whose count reaches K becomes the new upper end
+__global__ void k_fit_choose(FitState *st, int G, unsigned long long *hist, int64_t *next_len) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *next_len = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G; k += gridDim.x * blockDim.x) {
+        FitState s = st[k];
+        unsigned long long *h = hist + (size_t)k * 32;
+        int64_t step;
+        const int ni = fit_interior(s, step);
+        if (s.hi - s.lo <= 1) {
+            s.jsel = -1;
+        } else {
+            int64_t cum = s.base;
+            int chosen = ni;                    // the upper end always reaches K
+            for (int cc = 0; cc <= ni; ++cc) {
+                cum += (int64_t)h[cc];
+                if (cum >= s.K) { chosen = cc; break; }
+            }
+            for (int cc = 0; cc < chosen; ++cc) s.base += (int64_t)h[cc];
+            const int64_t nlo = chosen > 0 ? fit_point(s, chosen - 1) : s.lo;
+            const int64_t nhi = fit_point(s, chosen);
+            s.lo = nlo;
+            s.hi = nhi;
+            s.jsel = chosen;
+        }
+        for (int cc = 0; cc < 32; ++cc) h[cc] = 0;
+        st[k] = s;
+    }
+}
+
+// undecided edges of the next pass (order within the list does not matter: only counts are taken)
+__global__ void k_fit_compact(const int64_t *list, int64_t L, const int64_t *Ld, const uint8_t *cstar,
+                              const int64_t *goff_e, int G, const FitState *st, int64_t *out, int64_t *out_len) {
+    if (Ld) L = *Ld;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < L; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = list ? list[t] : t;
+        const int gph = G > 1 ? graph_of_edge(goff_e, G, e) : 0;
+        if ((int)cstar[t] == st[gph].jsel) out[atomicAdd((unsigned long long *)out_len, 1ull)] = e;
+    }
+}
+
 __global__ void k_keep_at(const int4 *info, const int32_t *tg, const int64_t *ts, const int64_t *te, const int32_t *T,
                           int32_t ndc, uint8_t *keep, unsigned long long *kept) {
     __shared__ unsigned long long sh[32];
@@ -592,13 +676,15 @@ struct ad_graph_s::SelCache {
     ad::Tiles tiles;
     bool have_tiles = false;
     bool have_lists = false;
-    int64_t *rows[6] = {};          // rows of rank classes 1..6
-    int64_t nrows[6] = {};
-    int64_t *brows = nullptr;       // (row, chunk) tasks of class 6
-    int32_t *bchunk = nullptr;
-    int64_t n_b = 0;
-    ad::DevBuf info, info_desc, ekey, skey, rank, T, hist, list_a, list_b, cstar, flag, jsel, kept, st, hist3, ties,
-        tie_off;
+    int64_t *rows[8] = {};          // rows of rank classes 1..8
+    int64_t nrows[8] = {};
+    int64_t *bstart = nullptr;      // class 8: first sorted slot of each row (nrows[7] + 1)
+    int64_t *bpos = nullptr;        // class 8 entries: CSR position and row slot
+    int32_t *bseg = nullptr;
+    int64_t nb_entries = 0;
+    ad::DevBuf info, info_desc, ekey, skey, bvals, T, hist, list_a, list_b, cstar, flag, jsel, kept, st, hist3, ties,
+        tie_off, ddeg, fit;
+    bool have_ddeg = false;       // ddeg: the distinct degrees on the device
     bool info_valid = false;      // info / info_desc hold the ranks of the handle's own distances
     uint64_t info_version = 0;
 };
@@ -625,29 +711,25 @@ static ad_status sel_cache(ad_graph_t g, ad_graph_s::SelCache **out) {
 static ad_status rank_lists(ad_graph_t g, ad_graph_s::SelCache *c) {
     if (c->have_lists) return AD_OK;
     const int64_t n = g->n;
+    constexpr int NC = kRankClasses - 1;
     uint8_t *flags = nullptr;
-    AD_TRY(dalloc_t(g, 6 * (n + 1), &flags));
+    AD_TRY(dalloc_t(g, NC * (n + 1), &flags));
     if (n > 0) AD_LAUNCH(k_rank_classes, g->num_sms * 8, 256, 0, g->stream, g->rp, n, flags);
-    for (int k = 0; k < 6; ++k) AD_TRY(compact_flags(g, flags + (int64_t)k * n, n, &c->rows[k], &c->nrows[k]));
-    const int64_t nbig = c->nrows[5];
-    if (nbig > 0) {   // few rows: expand (row, chunk) tasks on the host
-        std::vector<int64_t> rows(nbig);
-        AD_TRY(copy_out(g, rows.data(), c->rows[5], nbig * sizeof(int64_t)));
-        std::vector<int64_t> trow;
-        std::vector<int32_t> tch;
-        for (int64_t b = 0; b < nbig; ++b) {
-            int64_t r2[2];
-            AD_TRY(copy_out(g, r2, g->rp + rows[b], 2 * sizeof(int64_t)));
-            const int64_t nch = (r2[1] - r2[0] + kSortCap - 1) / kSortCap;
-            for (int64_t k = 0; k < nch; ++k) { trow.push_back(rows[b]); tch.push_back((int32_t)k); }
-        }
-        c->n_b = (int64_t)trow.size();
-        AD_TRY(dalloc_t(g, c->n_b, &c->brows));
-        AD_TRY(dalloc_t(g, c->n_b, &c->bchunk));
-        AD_TRY(copy_in(g, c->brows, trow.data(), c->n_b * sizeof(int64_t)));
-        AD_TRY(copy_in(g, c->bchunk, tch.data(), c->n_b * sizeof(int32_t)));
-    }
+    for (int k = 0; k < NC; ++k) AD_TRY(compact_flags(g, flags + (int64_t)k * n, n, &c->rows[k], &c->nrows[k]));
     dfree(g, flags);
+    const int64_t nbig = c->nrows[NC - 1];
+    if (nbig > 0) {
+        int64_t *deg = nullptr;
+        AD_TRY(dalloc_t(g, nbig + 1, &deg));
+        AD_TRY(dalloc_t(g, nbig + 1, &c->bstart));
+        AD_CUDA_TRY(cudaMemsetAsync(deg, 0, (nbig + 1) * sizeof(int64_t), g->stream));
+        AD_LAUNCH(k_row_degrees, (int)((nbig + 255) / 256), 256, 0, g->stream, c->rows[NC - 1], nbig, g->rp, deg);
+        AD_TRY(exclusive_scan_i64(g, deg, c->bstart, nbig + 1, &c->nb_entries));
+        dfree(g, deg);
+        AD_TRY(dalloc_t(g, c->nb_entries, &c->bpos));
+        AD_TRY(dalloc_t(g, c->nb_entries, &c->bseg));
+        AD_LAUNCH(k_big_expand, (int)nbig, 256, 0, g->stream, c->rows[NC - 1], g->rp, c->bstart, c->bpos, c->bseg);
+    }
     c->have_lists = true;
     return AD_OK;
 }
@@ -732,30 +814,41 @@ static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, i
         return (int)std::max<int64_t>(1, std::min<int64_t>((rows_ + 8 * per_warp - 1) / (8 * per_warp),
                                                            (int64_t)g->num_sms * 32));
     };
-    if (c->nrows[0] > 0)
-        AD_LAUNCH(k_rank_count<8>, wblocks(c->nrows[0], 4), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class,
-                  c->rows[0], c->nrows[0], ekey, out);
-    if (c->nrows[1] > 0)
-        AD_LAUNCH(k_rank_count<32>, wblocks(c->nrows[1], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class,
-                  c->rows[1], c->nrows[1], ekey, out);
-    if (c->nrows[2] > 0)
-        AD_LAUNCH(k_rank_wsort<4>, wblocks(c->nrows[2], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class,
-                  c->rows[2], c->nrows[2], ekey, out);
-    if (c->nrows[3] > 0)
-        AD_LAUNCH(k_rank_wsort<16>, wblocks(c->nrows[3], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class,
-                  c->rows[3], c->nrows[3], ekey, out);
-    if (c->nrows[4] > 0)
-        AD_LAUNCH(k_rank_mid, (int)c->nrows[4], 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, c->rows[4],
-                  ekey, out);
-    if (c->n_b > 0) {
-        AD_TRY(ensure(g, c->skey, sizeof(unsigned long long) * (nnz + 1)));
-        AD_TRY(ensure(g, c->rank, sizeof(uint32_t) * 3 * (nnz + 1)));
-        unsigned long long *skey = static_cast<unsigned long long *>(c->skey.ptr);
-        uint32_t *rank = static_cast<uint32_t *>(c->rank.ptr);
-        uint32_t *lt = rank + (nnz + 1), *leq = rank + 2 * (nnz + 1);
-        AD_LAUNCH(k_rank_chunks, (int)c->n_b, 512, 0, g->stream, g->rp, c->brows, c->bchunk, ekey, rank, lt, leq, skey);
-        AD_LAUNCH(k_rank_merge, (int)c->n_b, 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, c->brows,
-                  c->bchunk, ekey, skey, rank, lt, leq, out);
+    const int64_t *const *rows = c->rows;
+    const int64_t *nr = c->nrows;
+    if (nr[0] > 0)
+        AD_LAUNCH(k_rank_count<8>, wblocks(nr[0], 4), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[0],
+                  nr[0], ekey, out);
+    if (nr[1] > 0)
+        AD_LAUNCH(k_rank_count<32>, wblocks(nr[1], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[1],
+                  nr[1], ekey, out);
+    if (nr[2] > 0)
+        AD_LAUNCH(k_rank_wsort<2>, wblocks(nr[2], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[2],
+                  nr[2], ekey, out);
+    if (nr[3] > 0)
+        AD_LAUNCH(k_rank_wsort<4>, wblocks(nr[3], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[3],
+                  nr[3], ekey, out);
+    if (nr[4] > 0)
+        AD_LAUNCH(k_rank_wsort<8>, wblocks(nr[4], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[4],
+                  nr[4], ekey, out);
+    if (nr[5] > 0)
+        AD_LAUNCH(k_rank_wsort<16>, wblocks(nr[5], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[5],
+                  nr[5], ekey, out);
+    if (nr[6] > 0)
+        AD_LAUNCH(k_rank_mid, (int)nr[6], 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[6], ekey, out);
+    if (c->nb_entries > 0) {
+        const int64_t nb = c->nb_entries, nbig = nr[7];
+        AD_TRY(ensure(g, c->skey, sizeof(uint64_t) * nb));
+        AD_TRY(ensure(g, c->bvals, sizeof(int64_t) * nb));
+        uint64_t *keys = static_cast<uint64_t *>(c->skey.ptr);
+        int64_t *vals = static_cast<int64_t *>(c->bvals.ptr);
+        const int blocks = (int)std::min<int64_t>((nb + 255) / 256, (int64_t)g->num_sms * 16);
+        AD_LAUNCH(k_big_keys, blocks, 256, 0, g->stream, c->bpos, c->bseg, nb, ekey, keys, vals);
+        std::vector<int> shifts = {0, 8, 16, 24};          // the 32-bit key
+        for (int sh = 32; sh < 64 && ((nbig - 1) >> (sh - 32)) > 0; sh += 8) shifts.push_back(sh);   // row slot
+        AD_TRY(radix_sort_pairs(g, keys, vals, nb, shifts));
+        AD_LAUNCH(k_big_ranks, blocks, 256, 0, g->stream, keys, vals, nb, c->bstart, rows[7], g->eid, g->col,
+                  g->deg_class, out);
     }
     if (own) {
         c->info_valid = true;
@@ -804,10 +897,8 @@ ad_status select_per_node_at(ad_graph_t g, const float *score, double e, ad_mode
 // monotone in e).  Each pass counts the kept set at 15 interior points of the
 // current interval and its upper end; edges whose fate the chosen
 // sub-interval already decides drop out of the next pass.
-ad_status select_per_node_fit(ad_graph_t g, const float *score, double fraction, ad_mode mode, uint8_t *keep,
-                              int64_t *n_kept, double *e_used) {
-    int4 *info = nullptr;
-    AD_TRY(per_node_info(g, score, mode, &info));
+static ad_status select_per_node_fit_host(ad_graph_t g, const int4 *info, double fraction, uint8_t *keep,
+                                          int64_t *n_kept, double *e_used) {
     ad_graph_s::SelCache *c = g->sel;
     const int32_t ndc = std::max<int32_t>(g->n_deg_classes, 1);
     const int ncand = 16;   // 15 interior points + the upper end
@@ -864,7 +955,8 @@ ad_status select_per_node_fit(ad_graph_t g, const float *score, double fraction,
         AD_TRY(copy_in(g, T, Th.data(), Th.size() * sizeof(int32_t)));
         AD_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * G * 32, g->stream));
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((L + 255) / 256, (int64_t)g->num_sms * 16));
-        AD_LAUNCH(k_count_cand, blocks, 256, 0, g->stream, info, list, L, g->goff_e, G, T, ndc, ncand, hist, cstar);
+        AD_LAUNCH(k_count_cand, blocks, 256, 0, g->stream, info, list, L, (const int64_t *)nullptr, g->goff_e, G, T, ndc,
+                  ncand, hist, cstar);
         AD_TRY(copy_out(g, hh.data(), hist, sizeof(unsigned long long) * hh.size()));
         for (int32_t k = 0; k < G; ++k) {
             if (hi[k] - lo[k] <= 1) { jsel[k] = -1; continue; }
@@ -911,6 +1003,77 @@ ad_status select_per_node_fit(ad_graph_t g, const float *score, double fraction,
         if (hi[k] - lo[k] > 1) hi[k] = lo[k] + 1;
     std::vector<double> ev(G);
     for (int32_t k = 0; k < G; ++k) ev[k] = std::ldexp((double)hi[k], -40);
+    AD_TRY(keep_at(g, info, ev, keep, n_kept));
+    if (e_used) *e_used = G > 0 ? ev[0] : -1.0;
+    return AD_OK;
+}
+
+// The same search with every pass on the device; falls back to host tables
+// when a device T(d, e) is too close to a rounding boundary to be trusted.
+ad_status select_per_node_fit(ad_graph_t g, const float *score, double fraction, ad_mode mode, uint8_t *keep,
+                              int64_t *n_kept, double *e_used) {
+    int4 *info = nullptr;
+    AD_TRY(per_node_info(g, score, mode, &info));
+    ad_graph_s::SelCache *c = g->sel;
+    const int G = g->G;
+    const int32_t ndc = std::max<int32_t>(g->n_deg_classes, 1);
+    if (g->m == 0 || g->n_deg_classes == 0) return select_per_node_fit_host(g, info, fraction, keep, n_kept, e_used);
+    std::vector<FitState> sh(G);
+    for (int32_t k = 0; k < G; ++k) {
+        sh[k].lo = 0;
+        sh[k].hi = (int64_t)1 << 40;
+        sh[k].K = target_count(g->eoff_h[k + 1] - g->eoff_h[k], fraction);
+        sh[k].base = 0;
+        sh[k].jsel = -1;
+        sh[k].pad = 0;
+    }
+    if (!c->have_ddeg) {
+        AD_TRY(ensure(g, c->ddeg, sizeof(int64_t) * ndc));
+        AD_TRY(copy_in(g, c->ddeg.ptr, g->distinct_degrees.data(), sizeof(int64_t) * g->n_deg_classes));
+        c->have_ddeg = true;
+    }
+    AD_TRY(ensure(g, c->T, (size_t)G * kFitCand * ndc * sizeof(int32_t)));
+    AD_TRY(ensure(g, c->hist, (size_t)G * 32 * sizeof(unsigned long long)));
+    AD_TRY(ensure(g, c->cstar, (size_t)(g->m + 1)));
+    AD_TRY(ensure(g, c->list_a, sizeof(int64_t) * (g->m + 1)));
+    AD_TRY(ensure(g, c->list_b, sizeof(int64_t) * (g->m + 1)));
+    AD_TRY(ensure(g, c->fit, sizeof(FitState) * G + 4 * sizeof(int64_t)));
+    FitState *st = static_cast<FitState *>(c->fit.ptr);
+    int64_t *len = reinterpret_cast<int64_t *>(st + G);        // [0], [1]: list lengths; [2]: ambiguity flag
+    int *amb = reinterpret_cast<int *>(len + 2);
+    int32_t *T = static_cast<int32_t *>(c->T.ptr);
+    unsigned long long *hist = static_cast<unsigned long long *>(c->hist.ptr);
+    uint8_t *cstar = static_cast<uint8_t *>(c->cstar.ptr);
+    int64_t *lists[2] = {static_cast<int64_t *>(c->list_a.ptr), static_cast<int64_t *>(c->list_b.ptr)};
+    AD_TRY(copy_in(g, st, sh.data(), sizeof(FitState) * G));
+    AD_CUDA_TRY(cudaMemsetAsync(len, 0, 4 * sizeof(int64_t), g->stream));
+    AD_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)G * 32 * sizeof(unsigned long long), g->stream));
+    const int big = g->num_sms * 16;
+    const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)G * kFitCand * ndc + 255) / 256, big));
+    const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, big));
+    const int gblocks = (G + 255) / 256;
+    for (int pass = 0; pass < kFitPasses; ++pass) {
+        const int64_t *lin = pass == 0 ? nullptr : lists[pass & 1];
+        const int64_t *lin_len = pass == 0 ? nullptr : len + (pass & 1);
+        int64_t *lout = lists[(pass + 1) & 1], *lout_len = len + ((pass + 1) & 1);
+        AD_LAUNCH(k_fit_tables, tblocks, 256, 0, g->stream, st, G, static_cast<const int64_t *>(c->ddeg.ptr), ndc, T,
+                  amb);
+        AD_LAUNCH(k_count_cand, cblocks, 256, 0, g->stream, info, lin, g->m, lin_len, g->goff_e, G, T, ndc, kFitCand,
+                  hist, cstar);
+        AD_LAUNCH(k_fit_choose, gblocks, 256, 0, g->stream, st, G, hist, lout_len);
+        if (pass + 1 < kFitPasses)
+            AD_LAUNCH(k_fit_compact, cblocks, 256, 0, g->stream, lin, g->m, lin_len, cstar, g->goff_e, G, st, lout,
+                      lout_len);
+    }
+    AD_TRY(copy_out(g, sh.data(), st, sizeof(FitState) * G));
+    int amb_h = 0;
+    AD_TRY(copy_out(g, &amb_h, amb, sizeof(int)));
+    if (amb_h) return select_per_node_fit_host(g, info, fraction, keep, n_kept, e_used);
+    std::vector<double> ev(G);
+    for (int32_t k = 0; k < G; ++k) {
+        if (sh[k].hi - sh[k].lo > 1) return fail(AD_ERR_CUDA, "exponent search did not converge");
+        ev[k] = std::ldexp((double)sh[k].hi, -40);
+    }
     AD_TRY(keep_at(g, info, ev, keep, n_kept));
     if (e_used) *e_used = G > 0 ? ev[0] : -1.0;
     return AD_OK;

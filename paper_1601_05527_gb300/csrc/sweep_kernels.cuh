@@ -301,9 +301,9 @@ __device__ __forceinline__ void load_scale(const uint32_t *pmin, const uint32_t 
         for (int e = 0; e < V; ++e) {
             const int r = (gl + c * LPR) * V + e;
             float av = 1.f;
-            if (pmin) {
-                const double lo = ord2f(pmin[r]), hi = ord2f(pmax[r]);
-                av = hi > lo ? (float)(1.0 / (hi - lo)) : 0.f;
+            if (pmin) {   // FP32 on purpose: FP64 division runs on a very narrow pipe on this part
+                const float lo = ord2f(pmin[r]), hi = ord2f(pmax[r]);
+                av = hi > lo ? 1.f / (hi - lo) : 0.f;
             }
             A[c * V + e] = av;
         }
@@ -647,7 +647,6 @@ ad_status launch_distance(ad_graph_t g, const SweepArgs &a, int blocks) {
     AD_LAUNCH((k_distance<T, LPR, CPL>), blocks, 256, 0, g->stream, a);
     return AD_OK;
 }
-
 template <typename T, int LPR, int CPL>
 int blocks_for(bool sweep, size_t smem) {
     int per_sm = 0;
