@@ -18,6 +18,7 @@ a bounded sample of the same workload.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|bf16|fp16|q16]
     python bench.py --impl reference      # the FP64 CPU oracle, same metric
     python bench.py --scale 18 ...        # a smaller graph for profiler captures
+    python bench.py --workload ws512|ba2m|rmat22   # batched, multilevel, reverse-mode paths
 """
 from __future__ import annotations
 
@@ -217,13 +218,10 @@ def run_gpu(args):
             import torch.distributed as dist
             dist.barrier()
 
+    from paper_1601_05527_gb300 import replicas
+
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, dev)
 
     for _ in range(args.warmup):
         step(h, keep_d)
@@ -242,10 +240,10 @@ def run_gpu(args):
     barrier()
     launches = L.ad_kernel_launch_count() - launches0
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms = max_over_ranks(ms)
     units = g.nnz * R * K_SWEEPS
-    value = ws * args.steps * units / (ms / 1e3)
+    ms_local = ev0.elapsed_time(ev1)
+    value = replicas.whole_job_rate(args.steps * units, ms_local / 1e3, dev)   # all ranks' units / slowest rank
+    ms = max_over_ranks(ms_local)
 
     # the same step with 16-bit storage of the test vectors (FP32 accumulation), and its
     # accuracy against the FP32 path (itself within 1e-5 of the FP64 oracle)
@@ -353,6 +351,123 @@ def run_gpu(args):
     return 0
 
 
+def run_workload(args):
+    """The other workloads of the hot path, one JSON line each (not the headline):
+    ws512  -- 512 Watts-Strogatz graphs (n ~ U{1000..200000}, ring degree 10, p = 0.1) in one
+              batched handle, R = 16, k = 15, 16-bit storage, per-graph 25% global per-node
+              sparsification; compared with the plain form (FP32, one handle per graph);
+    ba2m   -- multilevel (Alg. 6) on Barabasi-Albert n = 2,000,000, m = 8, lognormal weights,
+              R = 16, k = 20, hierarchy to about 1,000 vertices, 40% at the coarse levels;
+    rmat22 -- reverse mode: R-MAT scale 22 with uniform(0.5, 2) weights, R = 32, k = 30,
+              loss over a seeded 1% edge subset, forward with checkpoints + backward."""
+    import torch
+    from paper_1601_05527_gb300 import build, graphgen, _lib as L
+    build.build()
+    L.load()
+    L.use_torch_allocator()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "ws512":
+        st = args.storage if args.storage != "fp32" else "bf16"
+        graphs = graphgen.ws_batch(512, seed=5)
+        voff, big = graphgen.concat(graphs)
+        h = L.ad_graph_create_batched(voff, big.n, torch.from_numpy(big.row_ptr).to(dev),
+                                      torch.from_numpy(big.col).to(dev), None, 0, stream)
+        keep = torch.empty(big.m, dtype=torch.uint8, device=dev)
+
+        def step():
+            L.ad_algebraic_distance(h, 16, 15, OMEGA, SEED, 0, st, 0, None)
+            L.ad_sparsify(h, 0.25, "global", "per_node", keep)
+        ms = timed(step, args.steps, args.warmup)
+        L.ad_graph_destroy(h)
+        hs = [L.ad_graph_create(gg.n, torch.from_numpy(gg.row_ptr).to(dev), torch.from_numpy(gg.col).to(dev), None,
+                                0, stream) for gg in graphs]
+        keeps = [torch.empty(gg.m, dtype=torch.uint8, device=dev) for gg in graphs]
+
+        def plain():
+            for hh, kk in zip(hs, keeps):
+                L.ad_algebraic_distance(hh, 16, 15, OMEGA, SEED, 0, "fp32", 0, None)
+                L.ad_sparsify(hh, 0.25, "global", "per_node", kk)
+        ms_plain = timed(plain, max(1, args.steps // 5), 1)
+        for hh in hs:
+            L.ad_graph_destroy(hh)
+        units = big.nnz * 16 * 15
+        line.update({"value": units / (ms / 1e3), "ms_per_step": ms, "dtype": f"{st} storage, f32 accumulate",
+                     "config": {"workload": "512 Watts-Strogatz graphs, n ~ U{1000..200000}, ring degree 10, p=0.1, "
+                                            "R=16, k=15, per-graph 25% global per-node sparsification, one batched handle",
+                                "n": big.n, "m": big.m, "nnz": big.nnz, "storage": st},
+                     "plain_fp32_one_handle_per_graph": {"value": units / (ms_plain / 1e3), "ms_per_step": ms_plain}})
+    elif args.workload == "ba2m":
+        g = graphgen.barabasi_albert(2_000_000, 8, seed=4)
+        g = graphgen.with_edge_weights(g, graphgen.lognormal_edge_weights(g.m, seed=4))
+        h = L.ad_graph_create(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                              torch.from_numpy(g.weight).to(dev), 0, stream)
+        keep = torch.empty(g.m, dtype=torch.uint8, device=dev)
+        info = {}
+
+        def step():
+            ml = L.ad_ml_build(h, R=16, k=20, omega=OMEGA, seed=SEED, Q=0.5, coarsest_n=1000, mode="local",
+                               storage=args.storage)
+            lv = L.ad_ml_levels(ml)
+            ratios = L.ad_ml_segment_ratios(lv, "coarse", max(1, lv // 3), 1.0)
+            info["kept"], info["r"] = L.ad_ml_sparsify(ml, ratios, 0.4, keep)
+            info["sizes"] = [L.ad_ml_level_size(ml, l) for l in range(lv)]
+            L.ad_ml_destroy(ml)
+        ms = timed(step, args.steps, args.warmup)
+        L.ad_graph_destroy(h)
+        units = sum(2 * m_l for _, m_l in info["sizes"]) * 16 * 20    # the sweeps of the downward pass
+        line.update({"value": units / (ms / 1e3), "ms_per_step": ms, "dtype": "f32" if args.storage == "fp32" else
+                     f"{args.storage} storage, f32 accumulate",
+                     "config": {"workload": "multilevel Alg. 6: Barabasi-Albert n=2,000,000 m=8, lognormal(0,1) weights, "
+                                            "R=16, k=20, Q=0.5, coarsest 1000, 40% controlled at the coarse third of levels",
+                                "levels": [list(x) for x in info["sizes"]], "kept": info["kept"], "ratio": info["r"],
+                                "units": "sum over levels of nnz_l*R*k of the downward pass"}})
+    elif args.workload == "rmat22":
+        g = graphgen.rmat(22, 16, seed=6)
+        ew = graphgen.uniform_edge_weights(g.m, seed=6)
+        g = graphgen.with_edge_weights(g, ew)
+        S = torch.from_numpy(graphgen.random_edge_subset(g.m, 0.01, seed=6)).to(dev)
+        h = L.ad_graph_create(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                              torch.from_numpy(g.weight).to(dev), 0, stream)
+        rho = torch.empty(g.m, dtype=torch.float32, device=dev)
+        rb = torch.zeros(g.m, dtype=torch.float32, device=dev)
+        wb = torch.empty(g.m, dtype=torch.float32, device=dev)
+
+        def fwd():
+            L.ad_algebraic_distance(h, 32, 30, OMEGA, SEED, 0, "fp32", L.AD_DIST_KEEP_STATE, rho)
+
+        def step():
+            fwd()
+            rb.index_copy_(0, S, 2.0 * rho.index_select(0, S))
+            L.ad_algebraic_distance_backward(h, rb, wb)
+        ms_fwd = timed(fwd, args.steps, args.warmup)
+        ms = timed(step, args.steps, args.warmup)
+        L.ad_graph_destroy(h)
+        units = g.nnz * 32 * 30
+        line.update({"value": units / (ms / 1e3), "ms_per_step": ms, "dtype": "f32",
+                     "config": {"workload": "reverse mode: R-MAT scale 22, uniform(0.5,2) weights, R=32, k=30, "
+                                            "loss = sum of rho^2 over a seeded 1% edge subset, sqrt(k) checkpoints",
+                                "n": g.n, "m": g.m, "nnz": g.nnz},
+                     "forward_with_checkpoints_ms": ms_fwd, "backward_ms": ms - ms_fwd})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global SCALE
     ap = argparse.ArgumentParser()
@@ -364,13 +479,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the 16-bit storage comparison")
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "ws512", "ba2m", "rmat22"],
+                    help="rmat20 is the benchmark; the others time the batched, multilevel and reverse-mode paths")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT scale; values other than 20 are smaller profiling cases, not the benchmark")
     args = ap.parse_args()
     SCALE = args.scale
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    return run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args) if args.workload == "rmat20" else run_workload(args)
 
 
 if __name__ == "__main__":

@@ -123,16 +123,6 @@ __global__ void k_check_rows(const int64_t *rp, int64_t n, int64_t nnz, unsigned
     }
 }
 
-// row of CSR position p (binary search in rp)
-__device__ __forceinline__ int64_t row_of(const int64_t *rp, int64_t n, int64_t p) {
-    int64_t lo = 0, hi = n;   // find largest i with rp[i] <= p
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (rp[mid] <= p) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ int64_t find_in_row(const int64_t *rp, const int32_t *col, int64_t r, int32_t c) {
     int64_t lo = rp[r], hi = rp[r + 1];
     while (lo < hi) {
@@ -142,11 +132,17 @@ __device__ __forceinline__ int64_t find_in_row(const int64_t *rp, const int32_t 
     return (lo < rp[r + 1] && col[lo] == c) ? lo : -1;
 }
 
-__global__ void k_check_entries(const int64_t *rp, const int32_t *col, const float *w, int64_t n, int64_t nnz,
-                                const int64_t *voff, int32_t G, unsigned long long *err) {
+__global__ void k_entry_rows(const int64_t *rp, int64_t n, int32_t *erow);
+
+// one thread per entry (row ids from k_entry_rows); records the mirror position
+// of every entry on the way, which the selection and the multilevel code reuse
+__global__ void k_check_entries(const int64_t *rp, const int32_t *col, const float *w, const int32_t *erow, int64_t n,
+                                int64_t nnz, const int64_t *voff, int32_t G, unsigned long long *err,
+                                int64_t *mirror) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = row_of(rp, n, p);
+        const int64_t i = erow[p];
         const int32_t j = col[p];
+        mirror[p] = -1;
         if (j < 0 || j >= n) { report(err, P_CSR, p); continue; }
         if (j == i) { report(err, P_SELF, p); continue; }
         if (p > rp[i] && col[p - 1] >= j) { report(err, P_DUP, p); continue; }
@@ -162,6 +158,7 @@ __global__ void k_check_entries(const int64_t *rp, const int32_t *col, const flo
         const int64_t q = find_in_row(rp, col, j, (int32_t)i);
         if (q < 0) { report(err, P_SYM, p); continue; }
         if (w && __float_as_uint(w[q]) != __float_as_uint(w[p])) report(err, P_SYM, p);
+        mirror[p] = q;
     }
 }
 
@@ -304,6 +301,13 @@ __global__ void k_count_active(const int64_t *rp, int64_t n, unsigned long long 
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
 }
 
+// out[k] = src[idx[k]] (idx[k] >= limit: fill); a handful of values read back with one copy
+__global__ void k_pick_i64(const int64_t *src, const int64_t *idx, int64_t count, int64_t limit, int64_t fill,
+                           int64_t *out) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < count) out[k] = idx[k] < limit ? src[idx[k]] : fill;
+}
+
 ad_status graph_setup(ad_graph_t g, int32_t flags) {
     const int64_t n = g->n;
     unsigned long long *err = nullptr;
@@ -315,8 +319,14 @@ ad_status graph_setup(ad_graph_t g, int32_t flags) {
         AD_LAUNCH(k_check_rows, grid, 256, 0, g->stream, g->rp, n, g->nnz, err);
         unsigned long long e0 = 0;
         AD_TRY(copy_out(g, &e0, err, sizeof(e0)));
-        if (e0 == ~0ull && g->nnz > 0)
-            AD_LAUNCH(k_check_entries, grid, 256, 0, g->stream, g->rp, g->col, g->w, n, g->nnz, g->voff, g->G, err);
+        if (e0 == ~0ull && g->nnz > 0) {   // row pointers are sound: row ids, then the entries
+            AD_TRY(dalloc_t(g, g->nnz, &g->erow));
+            AD_TRY(dalloc_t(g, g->nnz, &g->mirror));
+            const int64_t wblocks = std::min<int64_t>((n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
+            AD_LAUNCH(k_entry_rows, (int)wblocks, 256, 0, g->stream, g->rp, n, g->erow);
+            AD_LAUNCH(k_check_entries, g->num_sms * 16, 256, 0, g->stream, g->rp, g->col, g->w, g->erow, n, g->nnz,
+                      g->voff, g->G, err, g->mirror);
+        }
         AD_TRY(copy_out(g, &e0, err, sizeof(e0)));
         if (e0 != ~0ull) {
             const int prio = (int)(e0 >> 56);
@@ -336,27 +346,26 @@ ad_status graph_setup(ad_graph_t g, int32_t flags) {
     AD_TRY(dalloc_t(g, n + 1, &g->upos));
     AD_TRY(dalloc_t(g, n + 1, &g->eoff));
     AD_TRY(recompute_degrees(g));
-    // per-graph edge offsets
+    // per-graph edge offsets: the edge numbering at each graph's first vertex
     g->eoff_h.assign(g->G + 1, 0);
-    for (int32_t k = 0; k <= g->G; ++k) {
-        const int64_t v = g->voff_h[k];
-        if (v >= n) g->eoff_h[k] = g->m;
-        else AD_TRY(copy_out(g, &g->eoff_h[k], g->eoff + v, sizeof(int64_t)));
-    }
     AD_TRY(dalloc_t(g, g->G + 1, &g->goff_e));
-    AD_TRY(copy_in(g, g->goff_e, g->eoff_h.data(), sizeof(int64_t) * (g->G + 1)));
+    AD_LAUNCH(k_pick_i64, (g->G + 1 + 255) / 256, 256, 0, g->stream, g->eoff, g->voff, (int64_t)(g->G + 1), n, g->m,
+              g->goff_e);
+    AD_TRY(copy_out(g, g->eoff_h.data(), g->goff_e, sizeof(int64_t) * (g->G + 1)));
     return AD_OK;
 }
 
 ad_status ensure_mirror(ad_graph_t g) {
-    if (g->mirror || g->nnz == 0) return AD_OK;
-    AD_TRY(dalloc_t(g, g->nnz, &g->erow));
-    AD_TRY(dalloc_t(g, g->nnz, &g->mirror));
-    AD_TRY(dalloc_t(g, g->nnz, &g->eid));
-    const int64_t wblocks = std::min<int64_t>((g->n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
-    AD_LAUNCH(k_entry_rows, (int)wblocks, 256, 0, g->stream, g->rp, g->n, g->erow);
+    if (g->eid || g->nnz == 0) return AD_OK;
     const int grid = g->num_sms * 16;
-    AD_LAUNCH(k_mirror, grid, 256, 0, g->stream, g->rp, g->col, g->erow, g->nnz, g->mirror);
+    if (!g->mirror) {   // not recorded by validation (handles created without it)
+        AD_TRY(dalloc_t(g, g->nnz, &g->erow));
+        AD_TRY(dalloc_t(g, g->nnz, &g->mirror));
+        const int64_t wblocks = std::min<int64_t>((g->n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
+        AD_LAUNCH(k_entry_rows, (int)wblocks, 256, 0, g->stream, g->rp, g->n, g->erow);
+        AD_LAUNCH(k_mirror, grid, 256, 0, g->stream, g->rp, g->col, g->erow, g->nnz, g->mirror);
+    }
+    AD_TRY(dalloc_t(g, g->nnz, &g->eid));
     AD_LAUNCH(k_entry_eids, grid, 256, 0, g->stream, g->col, g->erow, g->upos, g->eoff, g->mirror, g->nnz, g->eid);
     return AD_OK;
 }
@@ -462,7 +471,19 @@ ad_status build_row_plan(ad_graph_t g, int groups, int small_max, bool upper_onl
     AD_LAUNCH(k_class_scatter, (int)tiles, kPartThreads, 0, g->stream, cls, n, offs, tiles, order);
     // class boundaries: offsets at tile 0 of each class
     std::vector<int64_t> start(kClasses + 1);
-    for (int c = 0; c < kClasses; ++c) AD_TRY(copy_out(g, &start[c], offs + (int64_t)c * tiles, sizeof(int64_t)));
+    {
+        std::vector<int64_t> at(kClasses);
+        for (int c = 0; c < kClasses; ++c) at[c] = (int64_t)c * tiles;
+        int64_t *at_d = nullptr, *picked = nullptr;
+        AD_TRY(dalloc_t(g, kClasses, &at_d));
+        AD_TRY(dalloc_t(g, kClasses, &picked));
+        AD_TRY(copy_in(g, at_d, at.data(), kClasses * sizeof(int64_t)));
+        AD_LAUNCH(k_pick_i64, 1, kClasses, 0, g->stream, offs, at_d, (int64_t)kClasses, (int64_t)kClasses * tiles,
+                  total, picked);
+        AD_TRY(copy_out(g, start.data(), picked, kClasses * sizeof(int64_t)));
+        dfree(g, at_d);
+        dfree(g, picked);
+    }
     start[kClasses] = total;
     const int64_t n_big_rows = start[1] - start[0];
     const int64_t n_med = start[11] - start[1];

@@ -231,26 +231,18 @@ __global__ void k_entry_keys(const int64_t *eid, int64_t nnz, const float *score
         ekey[p] = score_key(score[eid[p]], desc);
 }
 
-// The rank r of entry p of row i goes to its edge's info: (rank at the lower
-// endpoint, rank at the upper endpoint, degree class of each endpoint).
-__device__ __forceinline__ void put_rank(int4 *info, const int64_t *eid, const int32_t *col, const int32_t *dc,
-                                         int64_t i, int64_t p, uint32_t r) {
-    int *f = reinterpret_cast<int *>(info + eid[p]);
-    if (col[p] > i) { f[0] = (int)r; f[2] = dc[i]; }
-    else { f[1] = (int)r; f[3] = dc[i]; }
-}
-
-// Both orders from one ascending sort of (key, position): with lt / leq the
-// numbers of entries of the row with key < k / key <= k, the rank of an entry
-// in the descending order (ties still by ascending position) is
-// (d - leq) + (r_asc - lt).
+// Ranks are written per CSR entry in both orders; k_info then gathers them per
+// edge.  Both orders come from one ascending sort of (key, position): with lt
+// and leq the numbers of entries of the row with key < k and key <= k, the
+// rank of an entry in the descending order (ties still by ascending position)
+// is (d - leq) + (r_asc - lt).
 struct RankOut {
-    int4 *asc, *desc;
+    uint32_t *asc, *desc;
 };
-__device__ __forceinline__ void put_ranks(const RankOut &o, const int64_t *eid, const int32_t *col, const int32_t *dc,
-                                          int64_t i, int64_t p, int d, uint32_t r_asc, uint32_t lt, uint32_t leq) {
-    put_rank(o.asc, eid, col, dc, i, p, r_asc);
-    put_rank(o.desc, eid, col, dc, i, p, (uint32_t)d - leq + (r_asc - lt));
+__device__ __forceinline__ void put_ranks(const RankOut &o, int64_t p, int d, uint32_t r_asc, uint32_t lt,
+                                          uint32_t leq) {
+    o.asc[p] = r_asc;
+    o.desc[p] = (uint32_t)d - leq + (r_asc - lt);
 }
 
 constexpr int kSortCap = 2048;      // rows up to this degree are sorted by one CTA
@@ -258,8 +250,8 @@ constexpr int kSortCap = 2048;      // rows up to this degree are sorted by one 
 // rows of degree <= GS (8 or 32): a group of GS lanes per row, one entry per
 // lane, rank = number of smaller (key, position) pairs in the row
 template <int GS>
-__global__ void k_rank_count(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
-                             const int64_t *rows, int64_t nrows, const uint32_t *ekey, RankOut out) {
+__global__ void k_rank_count(const int64_t *rp, const int64_t *rows, int64_t nrows, const uint32_t *ekey,
+                             RankOut out) {
     const int lane = threadIdx.x & 31, sub = lane / GS, gl = lane % GS;
     const unsigned gmask = GS == 32 ? 0xffffffffu : (((1u << GS) - 1u) << (sub * GS));
     constexpr int RPW = 32 / GS;   // rows per warp
@@ -281,15 +273,14 @@ __global__ void k_rank_count(const int64_t *rp, const int32_t *col, const int64_
                 leq += o <= k ? 1u : 0u;
             }
         }
-        if (gl < d) put_ranks(out, eid, col, dc, i, p0 + gl, d, r, lt, leq);
+        if (gl < d) put_ranks(out, p0 + gl, d, r, lt, leq);
     }
 }
 
 // rows of degree <= 32 P: one warp sorts the row's (key, position) pairs in
 // registers (bitonic network over index lane * P + j), then writes the ranks
 template <int P>
-__global__ void __launch_bounds__(256) k_rank_wsort(const int64_t *rp, const int32_t *col, const int64_t *eid,
-                                                    const int32_t *dc, const int64_t *rows, int64_t nrows,
+__global__ void __launch_bounds__(256) k_rank_wsort(const int64_t *rp, const int64_t *rows, int64_t nrows,
                                                     const uint32_t *ekey, RankOut out) {
     constexpr int N = 32 * P;
     const int lane = threadIdx.x & 31;
@@ -375,7 +366,7 @@ __global__ void __launch_bounds__(256) k_rank_wsort(const int64_t *rp, const int
 #pragma unroll
         for (int j = 0; j < P; ++j)
             if (v[j] != ~0ull)
-                put_ranks(out, eid, col, dc, i, p0 + (int64_t)(v[j] & 0xffffffffull), d, (uint32_t)(lane * P + j),
+                put_ranks(out, p0 + (int64_t)(v[j] & 0xffffffffull), d, (uint32_t)(lane * P + j),
                           (uint32_t)first[j], (uint32_t)last[j] + 1);
     }
 }
@@ -406,8 +397,7 @@ __device__ __forceinline__ int lower_bound_smem(const unsigned long long *a, int
     return lo;
 }
 
-__global__ void k_rank_mid(const int64_t *rp, const int32_t *col, const int64_t *eid, const int32_t *dc,
-                           const int64_t *rows, const uint32_t *ekey, RankOut out) {
+__global__ void k_rank_mid(const int64_t *rp, const int64_t *rows, const uint32_t *ekey, RankOut out) {
     __shared__ unsigned long long a[kSortCap];
     const int64_t row = rows[blockIdx.x];
     const int64_t p0 = rp[row];
@@ -420,9 +410,12 @@ __global__ void k_rank_mid(const int64_t *rp, const int32_t *col, const int64_t 
     block_bitonic(a, len2);
     for (int t = threadIdx.x; t < d; t += blockDim.x) {
         const unsigned long long k32 = a[t] & 0xffffffff00000000ull;
-        const int lt = lower_bound_smem(a, d, k32);
-        const int leq = lower_bound_smem(a, d, k32 + 0x100000000ull);   // keys of real entries are < 2^32 - 1
-        put_ranks(out, eid, col, dc, row, p0 + (int64_t)(a[t] & 0xffffffffull), d, (uint32_t)t, (uint32_t)lt, (uint32_t)leq);
+        // tie runs need a search; a key unlike both neighbours is its own run
+        const int lt = (t > 0 && (a[t - 1] & 0xffffffff00000000ull) == k32) ? lower_bound_smem(a, d, k32) : t;
+        const int leq = (t + 1 < d && (a[t + 1] & 0xffffffff00000000ull) == k32)
+                            ? lower_bound_smem(a, d, k32 + 0x100000000ull)   // real keys are < 2^32 - 1
+                            : t + 1;
+        put_ranks(out, p0 + (int64_t)(a[t] & 0xffffffffull), d, (uint32_t)t, (uint32_t)lt, (uint32_t)leq);
     }
 }
 
@@ -453,7 +446,6 @@ __global__ void k_big_keys(const int64_t *bpos, const int32_t *bseg, int64_t nb,
 // first and last index of a run of equal keys give lt and leq (binary search
 // only where a neighbour holds the same key)
 __global__ void k_big_ranks(const uint64_t *keys, const int64_t *vals, int64_t nb, const int64_t *bstart,
-                            const int64_t *rows, const int64_t *eid, const int32_t *col, const int32_t *dc,
                             RankOut out) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nb; t += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = keys[t];
@@ -476,7 +468,7 @@ __global__ void k_big_ranks(const uint64_t *keys, const int64_t *vals, int64_t n
             }
             le = lo;
         }
-        put_ranks(out, eid, col, dc, rows[b], vals[t], (int)(e - s), (uint32_t)(t - s), (uint32_t)(lt - s),
+        put_ranks(out, vals[t], (int)(e - s), (uint32_t)(t - s), (uint32_t)(lt - s),
                   (uint32_t)(le - s));
     }
 }
@@ -484,6 +476,24 @@ __global__ void k_big_ranks(const uint64_t *keys, const int64_t *vals, int64_t n
 __global__ void k_row_degrees(const int64_t *rows, int64_t nrows, const int64_t *rp, int64_t *deg) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < nrows) deg[i] = rp[rows[i] + 1] - rp[rows[i]];
+}
+
+// upper CSR entry of every edge (built once per handle)
+__global__ void k_edge_pos(const int32_t *erow, const int32_t *col, const int64_t *eid, int64_t nnz, int64_t *epos) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        if (col[p] > erow[p]) epos[eid[p]] = p;
+}
+
+// per edge e = (i < j): (rank at i, rank at j, degree class of i, of j) in both orders
+__global__ void k_info(const int64_t *epos, const int64_t *mirror, const int32_t *erow, const int32_t *col,
+                       const int32_t *dc, int64_t m, const uint32_t *rasc, const uint32_t *rdesc, int4 *info_asc,
+                       int4 *info_desc) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = epos[e], q = mirror[p];
+        const int di = dc[erow[p]], dj = dc[col[p]];
+        info_asc[e] = make_int4((int)rasc[p], (int)rasc[q], di, dj);
+        info_desc[e] = make_int4((int)rdesc[p], (int)rdesc[q], di, dj);
+    }
 }
 
 // rank class of every row: 0 none, 1 d <= 8, 2 d <= 32, 3 d <= 64, 4 d <= 128, 5 d <= 256, 6 d <= 512,
@@ -515,20 +525,34 @@ __global__ void k_count_cand(const int4 *info, const int64_t *list, int64_t L, c
     if (threadIdx.x < 32) h[threadIdx.x] = 0;
     __syncthreads();
     if (Ld) L = *Ld;    // length of a list compacted on the device
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < L; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = list ? list[t] : t;
-        const int gph = G > 1 ? graph_of_edge(goff_e, G, e) : 0;
-        const int4 f = info[e];
-        const int32_t *Tg = T + (size_t)gph * nc * ndc;
-        int lo = 0, hi = nc;   // first candidate index (0-based) at which the edge is kept; nc = none
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const int32_t *Tm = Tg + (size_t)mid * ndc;
-            if (f.x < Tm[f.z] || f.y < Tm[f.w]) hi = mid; else lo = mid + 1;
+    const int lane = threadIdx.x & 31;
+    // warp-uniform trip count, so that the whole warp meets at the histogram update
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < L;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + lane;
+        int lo = 32;       // bin of a lane without an edge: never counted
+        int gph = 0;
+        if (t < L) {
+            const int64_t e = list ? list[t] : t;
+            gph = G > 1 ? graph_of_edge(goff_e, G, e) : 0;
+            const int4 f = info[e];
+            const int32_t *Tg = T + (size_t)gph * nc * ndc;
+            int l = 0, hi = nc;   // first candidate index (0-based) at which the edge is kept; nc = none
+            while (l < hi) {
+                const int mid = (l + hi) >> 1;
+                const int32_t *Tm = Tg + (size_t)mid * ndc;
+                if (f.x < Tm[f.z] || f.y < Tm[f.w]) hi = mid; else l = mid + 1;
+            }
+            cstar[t] = (uint8_t)l;
+            lo = l;
         }
-        cstar[t] = (uint8_t)lo;
-        if (G == 1) atomicAdd(&h[lo], 1u);
-        else atomicAdd(hist + (size_t)gph * 32 + lo, 1ull);
+        if (G == 1) {
+            // lanes with the same bin add once (few bins, so shared-memory atomics would serialise)
+            const unsigned peers = __match_any_sync(0xffffffffu, lo);
+            if (lo < 32 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[lo], (unsigned)__popc(peers));
+        } else if (lo < 32) {
+            atomicAdd(hist + (size_t)gph * 32 + lo, 1ull);
+        }
     }
     __syncthreads();
     if (G == 1 && threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(hist + threadIdx.x, (unsigned long long)h[threadIdx.x]);
@@ -580,17 +604,29 @@ __device__ __forceinline__ int64_t fit_point(const FitState &s, int cc) {
     return cc < ni ? s.lo + step * (cc + 1) : s.hi;
 }
 
-__global__ void k_fit_tables(const FitState *st, int G, const int64_t *ddeg, int32_t ndc, int32_t *T, int *ambiguous) {
+// T of every (graph, candidate, degree class).  Tlo / Thi hold T at the ends
+// of the graph's current interval; T is monotone in e, so a class with equal
+// ends is constant inside and needs no pow.
+__global__ void k_fit_tables(const FitState *st, int G, const int64_t *ddeg, int32_t ndc, const int32_t *Tlo,
+                             const int32_t *Thi, int32_t *T, int *ambiguous) {
     const int64_t total = (int64_t)G * kFitCand * ndc;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int q = (int)(idx % ndc);
         const int64_t kc = idx / ndc;
         const int cc = (int)(kc % kFitCand), k = (int)(kc / kFitCand);
-        const int64_t d = ddeg[q];
-        int32_t t = 0;
-        if (d > 0) {
-            const double e = ldexp((double)fit_point(st[k], cc), -40);
+        const FitState s = st[k];
+        int64_t step;
+        const int ni = fit_interior(s, step);
+        const int32_t tl = Tlo[(size_t)k * ndc + q], th = Thi[(size_t)k * ndc + q];
+        int32_t t;
+        if (cc >= ni) {
+            t = th;                              // the upper end
+        } else if (tl == th) {
+            t = tl;
+        } else {
+            const int64_t d = ddeg[q];
+            const double e = ldexp((double)(s.lo + step * (cc + 1)), -40);
             const double v = pow((double)d, e);
             const double x = v - 1e-9;
             const double f = x - floor(x);
@@ -602,6 +638,30 @@ __global__ void k_fit_tables(const FitState *st, int G, const int64_t *ddeg, int
             t = (int32_t)c;
         }
         T[idx] = t;
+    }
+}
+
+// T at the ends of the new interval: the tables of the chosen point and of the one before it
+__global__ void k_fit_bounds(const FitState *st, int G, int32_t ndc, const int32_t *T, int32_t *Tlo, int32_t *Thi) {
+    const int64_t total = (int64_t)G * ndc;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx / ndc), q = (int)(idx % ndc);
+        const int chosen = st[k].jsel;
+        if (chosen < 0) continue;
+        if (chosen > 0) Tlo[idx] = T[((size_t)k * kFitCand + chosen - 1) * ndc + q];
+        Thi[idx] = T[((size_t)k * kFitCand + chosen) * ndc + q];
+    }
+}
+
+// initial ends: e = 0 keeps one edge per node, e = 1 all of them
+__global__ void k_fit_init_bounds(int G, const int64_t *ddeg, int32_t ndc, int32_t *Tlo, int32_t *Thi) {
+    const int64_t total = (int64_t)G * ndc;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = ddeg[idx % ndc];
+        Tlo[idx] = d > 0 ? 1 : 0;
+        Thi[idx] = (int32_t)d;
     }
 }
 
@@ -634,14 +694,58 @@ __global__ void k_fit_choose(FitState *st, int G, unsigned long long *hist, int6
     }
 }
 
-// undecided edges of the next pass (order within the list does not matter: only counts are taken)
-__global__ void k_fit_compact(const int64_t *list, int64_t L, const int64_t *Ld, const uint8_t *cstar,
-                              const int64_t *goff_e, int G, const FitState *st, int64_t *out, int64_t *out_len) {
+// undecided edges of the next pass (order within the list does not matter:
+// only counts are taken).  One atomic per block and tile: a single counter
+// takes millions of survivors in the first pass.
+constexpr int kCompactItems = 4;   // elements per thread per tile
+__global__ void __launch_bounds__(256) k_fit_compact(const int64_t *list, int64_t L, const int64_t *Ld,
+                                                     const uint8_t *cstar, const int64_t *goff_e, int G,
+                                                     const FitState *st, int64_t *out, int64_t *out_len) {
+    __shared__ unsigned int wcount[8];
+    __shared__ unsigned long long base_sh;
     if (Ld) L = *Ld;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < L; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = list ? list[t] : t;
-        const int gph = G > 1 ? graph_of_edge(goff_e, G, e) : 0;
-        if ((int)cstar[t] == st[gph].jsel) out[atomicAdd((unsigned long long *)out_len, 1ull)] = e;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t tile = (int64_t)blockDim.x * kCompactItems;
+    for (int64_t t0 = blockIdx.x * tile; t0 < L; t0 += (int64_t)gridDim.x * tile) {
+        bool take[kCompactItems];
+        int64_t ev[kCompactItems];
+        unsigned mine = 0;
+#pragma unroll
+        for (int u = 0; u < kCompactItems; ++u) {
+            const int64_t t = t0 + (int64_t)u * blockDim.x + threadIdx.x;
+            take[u] = false;
+            ev[u] = 0;
+            if (t < L) {
+                ev[u] = list ? list[t] : t;
+                const int gph = G > 1 ? graph_of_edge(goff_e, G, ev[u]) : 0;
+                take[u] = (int)cstar[t] == st[gph].jsel;
+            }
+            mine += take[u] ? 1u : 0u;
+        }
+        // exclusive prefix of `mine` over the block: warp scan, then warp totals
+        unsigned incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wcount[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const unsigned c = wcount[w];
+                wcount[w] = tot;
+                tot += c;
+            }
+            base_sh = tot ? atomicAdd((unsigned long long *)out_len, (unsigned long long)tot) : 0ull;
+        }
+        __syncthreads();
+        unsigned long long pos = base_sh + wcount[warp] + (incl - mine);
+#pragma unroll
+        for (int u = 0; u < kCompactItems; ++u)
+            if (take[u]) out[pos++] = ev[u];
+        __syncthreads();
     }
 }
 
@@ -683,7 +787,8 @@ struct ad_graph_s::SelCache {
     int32_t *bseg = nullptr;
     int64_t nb_entries = 0;
     ad::DevBuf info, info_desc, ekey, skey, bvals, T, hist, list_a, list_b, cstar, flag, jsel, kept, st, hist3, ties,
-        tie_off, ddeg, fit;
+        tie_off, ddeg, fit, fit_tb, rank2;
+    int64_t *epos = nullptr;      // upper CSR entry of every edge
     bool have_ddeg = false;       // ddeg: the distinct degrees on the device
     bool info_valid = false;      // info / info_desc hold the ranks of the handle's own distances
     uint64_t info_version = 0;
@@ -800,13 +905,20 @@ static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, i
     const int64_t nnz = g->nnz;
     AD_TRY(ensure(g, c->info, sizeof(int4) * (g->m + 1)));
     AD_TRY(ensure(g, c->info_desc, sizeof(int4) * (g->m + 1)));
-    RankOut out;
-    out.asc = static_cast<int4 *>(c->info.ptr);
-    out.desc = static_cast<int4 *>(c->info_desc.ptr);
-    *info_out = mode == AD_MODE_GLOBAL ? out.desc : out.asc;
+    int4 *info_asc = static_cast<int4 *>(c->info.ptr), *info_desc = static_cast<int4 *>(c->info_desc.ptr);
+    *info_out = mode == AD_MODE_GLOBAL ? info_desc : info_asc;
     const bool own = score == g->rho && g->have_rho;
     if (own && c->info_valid && c->info_version == g->rho_version) return AD_OK;
     c->info_valid = false;
+    if (!c->epos) {
+        AD_TRY(dalloc_t(g, g->m + 1, &c->epos));
+        if (nnz > 0)
+            AD_LAUNCH(k_edge_pos, g->num_sms * 16, 256, 0, g->stream, g->erow, g->col, g->eid, nnz, c->epos);
+    }
+    AD_TRY(ensure(g, c->rank2, 2 * sizeof(uint32_t) * (nnz + 1)));
+    RankOut out;
+    out.asc = static_cast<uint32_t *>(c->rank2.ptr);
+    out.desc = out.asc + (nnz + 1);
     AD_TRY(ensure(g, c->ekey, sizeof(uint32_t) * (nnz + 1)));
     uint32_t *ekey = static_cast<uint32_t *>(c->ekey.ptr);
     if (nnz > 0) AD_LAUNCH(k_entry_keys, g->num_sms * 16, 256, 0, g->stream, g->eid, nnz, score, 0, ekey);
@@ -817,25 +929,25 @@ static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, i
     const int64_t *const *rows = c->rows;
     const int64_t *nr = c->nrows;
     if (nr[0] > 0)
-        AD_LAUNCH(k_rank_count<8>, wblocks(nr[0], 4), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[0],
+        AD_LAUNCH(k_rank_count<8>, wblocks(nr[0], 4), 256, 0, g->stream, g->rp, rows[0],
                   nr[0], ekey, out);
     if (nr[1] > 0)
-        AD_LAUNCH(k_rank_count<32>, wblocks(nr[1], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[1],
+        AD_LAUNCH(k_rank_count<32>, wblocks(nr[1], 1), 256, 0, g->stream, g->rp, rows[1],
                   nr[1], ekey, out);
     if (nr[2] > 0)
-        AD_LAUNCH(k_rank_wsort<2>, wblocks(nr[2], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[2],
+        AD_LAUNCH(k_rank_wsort<2>, wblocks(nr[2], 1), 256, 0, g->stream, g->rp, rows[2],
                   nr[2], ekey, out);
     if (nr[3] > 0)
-        AD_LAUNCH(k_rank_wsort<4>, wblocks(nr[3], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[3],
+        AD_LAUNCH(k_rank_wsort<4>, wblocks(nr[3], 1), 256, 0, g->stream, g->rp, rows[3],
                   nr[3], ekey, out);
     if (nr[4] > 0)
-        AD_LAUNCH(k_rank_wsort<8>, wblocks(nr[4], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[4],
+        AD_LAUNCH(k_rank_wsort<8>, wblocks(nr[4], 1), 256, 0, g->stream, g->rp, rows[4],
                   nr[4], ekey, out);
     if (nr[5] > 0)
-        AD_LAUNCH(k_rank_wsort<16>, wblocks(nr[5], 1), 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[5],
+        AD_LAUNCH(k_rank_wsort<16>, wblocks(nr[5], 1), 256, 0, g->stream, g->rp, rows[5],
                   nr[5], ekey, out);
     if (nr[6] > 0)
-        AD_LAUNCH(k_rank_mid, (int)nr[6], 256, 0, g->stream, g->rp, g->col, g->eid, g->deg_class, rows[6], ekey, out);
+        AD_LAUNCH(k_rank_mid, (int)nr[6], 256, 0, g->stream, g->rp, rows[6], ekey, out);
     if (c->nb_entries > 0) {
         const int64_t nb = c->nb_entries, nbig = nr[7];
         AD_TRY(ensure(g, c->skey, sizeof(uint64_t) * nb));
@@ -847,9 +959,11 @@ static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, i
         std::vector<int> shifts = {0, 8, 16, 24};          // the 32-bit key
         for (int sh = 32; sh < 64 && ((nbig - 1) >> (sh - 32)) > 0; sh += 8) shifts.push_back(sh);   // row slot
         AD_TRY(radix_sort_pairs(g, keys, vals, nb, shifts));
-        AD_LAUNCH(k_big_ranks, blocks, 256, 0, g->stream, keys, vals, nb, c->bstart, rows[7], g->eid, g->col,
-                  g->deg_class, out);
+        AD_LAUNCH(k_big_ranks, blocks, 256, 0, g->stream, keys, vals, nb, c->bstart, out);
     }
+    if (g->m > 0)
+        AD_LAUNCH(k_info, g->num_sms * 16, 256, 0, g->stream, c->epos, g->mirror, g->erow, g->col, g->deg_class, g->m,
+                  out.asc, out.desc, info_asc, info_desc);
     if (own) {
         c->info_valid = true;
         c->info_version = g->rho_version;
@@ -1038,6 +1152,8 @@ ad_status select_per_node_fit(ad_graph_t g, const float *score, double fraction,
     AD_TRY(ensure(g, c->list_a, sizeof(int64_t) * (g->m + 1)));
     AD_TRY(ensure(g, c->list_b, sizeof(int64_t) * (g->m + 1)));
     AD_TRY(ensure(g, c->fit, sizeof(FitState) * G + 4 * sizeof(int64_t)));
+    AD_TRY(ensure(g, c->fit_tb, 2 * sizeof(int32_t) * (size_t)G * ndc));
+    int32_t *Tlo = static_cast<int32_t *>(c->fit_tb.ptr), *Thi = Tlo + (size_t)G * ndc;
     FitState *st = static_cast<FitState *>(c->fit.ptr);
     int64_t *len = reinterpret_cast<int64_t *>(st + G);        // [0], [1]: list lengths; [2]: ambiguity flag
     int *amb = reinterpret_cast<int *>(len + 2);
@@ -1052,15 +1168,19 @@ ad_status select_per_node_fit(ad_graph_t g, const float *score, double fraction,
     const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)G * kFitCand * ndc + 255) / 256, big));
     const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, big));
     const int gblocks = (G + 255) / 256;
+    const int bblocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)G * ndc + 255) / 256, big));
+    AD_LAUNCH(k_fit_init_bounds, bblocks, 256, 0, g->stream, G, static_cast<const int64_t *>(c->ddeg.ptr), ndc, Tlo,
+              Thi);
     for (int pass = 0; pass < kFitPasses; ++pass) {
         const int64_t *lin = pass == 0 ? nullptr : lists[pass & 1];
         const int64_t *lin_len = pass == 0 ? nullptr : len + (pass & 1);
         int64_t *lout = lists[(pass + 1) & 1], *lout_len = len + ((pass + 1) & 1);
-        AD_LAUNCH(k_fit_tables, tblocks, 256, 0, g->stream, st, G, static_cast<const int64_t *>(c->ddeg.ptr), ndc, T,
-                  amb);
+        AD_LAUNCH(k_fit_tables, tblocks, 256, 0, g->stream, st, G, static_cast<const int64_t *>(c->ddeg.ptr), ndc, Tlo,
+                  Thi, T, amb);
         AD_LAUNCH(k_count_cand, cblocks, 256, 0, g->stream, info, lin, g->m, lin_len, g->goff_e, G, T, ndc, kFitCand,
                   hist, cstar);
         AD_LAUNCH(k_fit_choose, gblocks, 256, 0, g->stream, st, G, hist, lout_len);
+        if (pass + 1 < kFitPasses) AD_LAUNCH(k_fit_bounds, bblocks, 256, 0, g->stream, st, G, ndc, T, Tlo, Thi);
         if (pass + 1 < kFitPasses)
             AD_LAUNCH(k_fit_compact, cblocks, 256, 0, g->stream, lin, g->m, lin_len, cstar, g->goff_e, G, st, lout,
                       lout_len);

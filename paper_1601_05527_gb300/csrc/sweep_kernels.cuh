@@ -558,10 +558,10 @@ __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64
                 v[u][c] = (pb + (int64_t)u * step < p1 && q < a.nchunks) ? __ldg(X + (int64_t)jn[u] * row_q + q)
                                                                           : make_uint4(0, 0, 0, 0);
             }
+        float s[UB];
 #pragma unroll
         for (int u = 0; u < UB; ++u) {
-            const int64_t p = pb + (int64_t)u * step;
-            float s = 0.f;
+            s[u] = 0.f;
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 float yj[V];
@@ -569,14 +569,44 @@ __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
                     const float d = yi[c * V + e] - yj[e];
-                    s = fmaf(A2[c * V + e] * d, d, s);
+                    s[u] = fmaf(A2[c * V + e] * d, d, s[u]);
                 }
             }
+        }
+        // sums over the group's lanes, transposed: each exchange halves the
+        // values a lane holds, so UB sums take about LPR shuffles in total
+        // instead of UB * log2(LPR); afterwards lane gl holds the sums of
+        // edges which .. which + NH - 1
+        constexpr int NH = UB / LPR > 0 ? UB / LPR : 1;
+        int which = 0;
 #pragma unroll
-            for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
-            if (gl == 0 && p < p1) {
-                float rho = sqrtf(s);
-                if (a.normalize) rho = (float)((double)rho * sqrt(Di * a.D[jn[u]]));
+        for (int o = LPR / 2, c = UB; o >= 1; o >>= 1) {
+            if (c > 1) {
+                const bool upper = (gl & o) != 0;
+#pragma unroll
+                for (int i = 0; i < UB / 2; ++i) {
+                    if (i < c / 2) {
+                        const float send = upper ? s[i] : s[i + c / 2];
+                        const float keep = upper ? s[i + c / 2] : s[i];
+                        s[i] = keep + __shfl_xor_sync(gmask, send, o);
+                    }
+                }
+                if (upper) which += c / 2;
+                c >>= 1;
+            } else {
+                s[0] += __shfl_xor_sync(gmask, s[0], o);
+            }
+        }
+        const bool writer = (LPR <= UB) || (gl % (LPR / UB) == 0);
+#pragma unroll
+        for (int i = 0; i < NH; ++i) {
+            int32_t jw = 0;
+#pragma unroll
+            for (int u = 0; u < UB; ++u) jw = (u == which + i) ? jn[u] : jw;
+            const int64_t p = pb + (int64_t)(which + i) * step;
+            if (writer && p < p1) {
+                float rho = sqrtf(s[i]);
+                if (a.normalize) rho = (float)((double)rho * sqrt(Di * a.D[jw]));
                 a.rho[ebase + p] = rho;
             }
         }
