@@ -273,7 +273,7 @@ struct ad_graph_s {
     uint64_t rho_version = 0;    // bumped whenever rho is recomputed
 
     // cached scratch
-    ad::DevBuf x0, x1, part, mm, ws;
+    ad::DevBuf x0, x1, part, mm, ws, ac;
 
     // profiling
     bool profiling = false;
@@ -289,6 +289,19 @@ struct ad_graph_s {
     struct SelCache;
     SelCache *sel = nullptr;
     ad::DevBuf scan_ws;
+
+    // CUDA graph of the launch sequence of a repeated ad_algebraic_distance call
+    struct Replay {
+        bool have_key = false;      // key / ptrs describe the last call
+        int32_t R = 0, k = 0, flags = 0;
+        double omega = 0;
+        uint64_t seed = 0;
+        uint32_t stream_id = 0;
+        int32_t storage = 0;
+        const void *ptrs[7] = {};   // scratch the launches read or write (x0, x1, mm, ac, part, rho, plans)
+        cudaGraphExec_t exec = nullptr;
+        uint64_t launches = 0;      // kernels in the graph
+    } replay;
 };
 
 namespace ad {

@@ -102,12 +102,12 @@ struct BwArgs {
     float omega;
     // distance backward
     const float *rho, *rhobar;
-    float a_k[256];              // per-vector scale of the last iterate
+    const float *a_k;            // [stride] per-vector scale of the last iterate (device)
     // sweep backward
     const float *U;              // D^-1 ybar_t
     const float *Sprev;          // stored s_{t-1}
     const float *Ybar;           // ybar_t
-    float a_prev[256];           // a_{t-1} (1 for t = 1)
+    const float *a_prev;         // [stride] a_{t-1} (device; nullptr: 1, for t = 1)
     const float *Sk;             // stored s_k (distance backward input)
     float *xbar_out;
     double *G;                   // [nnz]
@@ -126,17 +126,26 @@ __device__ __forceinline__ void ld4(const float *base, int64_t row, int stride, 
     out[0] = f.x; out[1] = f.y; out[2] = f.z; out[3] = f.w;
 }
 
+template <int LPR, int CPL>
+__device__ __forceinline__ void bw_gather_adjoint(const BwArgs &a, int64_t p0, int64_t p1, int first, int gstride,
+                                                  int gl, unsigned gmask, const float (&v)[CPL * 4],
+                                                  float (&acc_a)[CPL * 4], float (&acc_b)[CPL * 4]);
+
 // One row (or chunk of a row) p in [p0, p1) processed by the warp (G groups
 // over neighbours) or by one group (G = 1 group, gstride = 1).
 //   mode 0: acc_a = sum c_p s_j, acc_b = sum c_p (scalar in slot 0)
-//   mode 1: acc_a = sum w U_j, acc_b = sum w s_j, G_p += v_i . s_j
+//   mode 1: acc_a = sum w U_j, acc_b = sum w s_j, G_p += v_i . s_j (bw_gather_adjoint)
 template <int LPR, int CPL>
 __device__ __forceinline__ void bw_gather(const BwArgs &a, int64_t row, int64_t p0, int64_t p1, int first, int gstride,
                                           int gl, unsigned gmask, const float (&v)[CPL * 4], float (&acc_a)[CPL * 4],
                                           float (&acc_b)[CPL * 4]) {
+    if (a.mode == 1) {
+        bw_gather_adjoint<LPR, CPL>(a, p0, p1, first, gstride, gl, gmask, v, acc_a, acc_b);
+        return;
+    }
     for (int64_t p = p0 + first; p < p1; p += gstride) {
         const int32_t j = __ldg(a.col + p);
-        if (a.mode == 0) {
+        {
             const int64_t e = a.eid[p];
             const float r = a.rho[e];
             const float cf = r > 0.f ? a.rhobar[e] / r : 0.f;
@@ -151,27 +160,68 @@ __device__ __forceinline__ void bw_gather(const BwArgs &a, int64_t row, int64_t 
                 }
             }
             acc_b[0] += cf;
-        } else {
-            const float wt = a.w ? __ldg(a.w + p) : 1.f;
-            float dot = 0.f;
+        }
+    }
+}
+
+// mode 1 in batches of kBwUB neighbours per group: all their loads are issued
+// before any is used, and the per-entry dots are summed over the group's lanes
+// together (group_sums)
+#ifndef AD_BW_UB
+#define AD_BW_UB 4
+#endif
+constexpr int kBwUB = AD_BW_UB;
+template <int LPR, int CPL>
+__device__ __forceinline__ void bw_gather_adjoint(const BwArgs &a, int64_t p0, int64_t p1, int first, int gstride,
+                                                  int gl, unsigned gmask, const float (&v)[CPL * 4],
+                                                  float (&acc_a)[CPL * 4], float (&acc_b)[CPL * 4]) {
+    constexpr int UB = kBwUB;
+    for (int64_t pb = p0 + first; pb < p1; pb += (int64_t)gstride * UB) {
+        int32_t jn[UB];
+        float wt[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int64_t p = pb + (int64_t)u * gstride;
+            const bool ok = p < p1;
+            jn[u] = ok ? __ldg(a.col + p) : 0;
+            wt[u] = ok ? (a.w ? __ldg(a.w + p) : 1.f) : 0.f;
+        }
+        float4 uu[UB][CPL], ss[UB][CPL];
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 const int q = gl + c * LPR;
-                if (q < a.nchunks) {
-                    float u[4], s[4];
-                    ld4<CPL>(a.U, j, a.stride, q, u);
-                    ld4<CPL>(a.Sprev, j, a.stride, q, s);
+                const bool ok = pb + (int64_t)u * gstride < p1 && q < a.nchunks;
+                uu[u][c] = ok ? __ldg(reinterpret_cast<const float4 *>(a.U + (int64_t)jn[u] * a.stride) + q)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                ss[u][c] = ok ? __ldg(reinterpret_cast<const float4 *>(a.Sprev + (int64_t)jn[u] * a.stride) + q)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        float dot[UB];
 #pragma unroll
-                    for (int e4 = 0; e4 < 4; ++e4) {
-                        acc_a[c * 4 + e4] = fmaf(wt, u[e4], acc_a[c * 4 + e4]);
-                        acc_b[c * 4 + e4] = fmaf(wt, s[e4], acc_b[c * 4 + e4]);
-                        dot = fmaf(v[c * 4 + e4], s[e4], dot);
-                    }
+        for (int u = 0; u < UB; ++u) {
+            dot[u] = 0.f;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                const float uf[4] = {uu[u][c].x, uu[u][c].y, uu[u][c].z, uu[u][c].w};
+                const float sf[4] = {ss[u][c].x, ss[u][c].y, ss[u][c].z, ss[u][c].w};
+#pragma unroll
+                for (int e4 = 0; e4 < 4; ++e4) {
+                    acc_a[c * 4 + e4] = fmaf(wt[u], uf[e4], acc_a[c * 4 + e4]);
+                    acc_b[c * 4 + e4] = fmaf(wt[u], sf[e4], acc_b[c * 4 + e4]);
+                    dot[u] = fmaf(v[c * 4 + e4], sf[e4], dot[u]);
                 }
             }
+        }
+        int which = 0;
+        group_sums<LPR, UB>(dot, gl, gmask, which);
+        constexpr int NH = UB / LPR > 0 ? UB / LPR : 1;
+        const bool writer = (LPR <= UB) || (gl % (LPR / UB) == 0);
 #pragma unroll
-            for (int off = 1; off < LPR; off <<= 1) dot += __shfl_xor_sync(gmask, dot, off);
-            if (gl == 0) a.G[p] += (double)dot;
+        for (int i = 0; i < NH; ++i) {
+            const int64_t p = pb + (int64_t)(which + i) * gstride;
+            if (writer && p < p1) a.G[p] += (double)dot[i];
         }
     }
 }
@@ -191,7 +241,7 @@ __device__ __forceinline__ void bw_finish(const BwArgs &a, int64_t row, int gl, 
 #pragma unroll
                 for (int e4 = 0; e4 < 4; ++e4) {
                     const int r = q * 4 + e4;
-                    xo[r] = a.a_k[r] * (csum * own[c * 4 + e4] - acc_a[c * 4 + e4]);
+                    xo[r] = (r < a.R ? __ldg(a.a_k + r) : 0.f) * (csum * own[c * 4 + e4] - acc_a[c * 4 + e4]);
                 }
             }
         }
@@ -226,7 +276,8 @@ __device__ __forceinline__ void bw_own(const BwArgs &a, int64_t row, int gl, flo
         if (q < a.nchunks) {
             ld4<CPL>(a.mode == 0 ? a.Sk : a.Ybar, row, a.stride, q, own + c * 4);
 #pragma unroll
-            for (int e4 = 0; e4 < 4; ++e4) v[c * 4 + e4] = a.mode == 1 ? own[c * 4 + e4] * a.a_prev[q * 4 + e4] : 0.f;
+            for (int e4 = 0; e4 < 4; ++e4)
+                v[c * 4 + e4] = a.mode == 1 ? own[c * 4 + e4] * (a.a_prev ? __ldg(a.a_prev + q * 4 + e4) : 1.f) : 0.f;
         } else {
 #pragma unroll
             for (int e4 = 0; e4 < 4; ++e4) { own[c * 4 + e4] = 0.f; v[c * 4 + e4] = 0.f; }
@@ -234,8 +285,11 @@ __device__ __forceinline__ void bw_own(const BwArgs &a, int64_t row, int gl, flo
     }
 }
 
+#ifndef AD_BW_MINB
+#define AD_BW_MINB 1
+#endif
 template <int LPR, int CPL>
-__global__ void __launch_bounds__(256) k_bw(BwArgs a) {
+__global__ void __launch_bounds__(256, AD_BW_MINB) k_bw(BwArgs a) {
     constexpr int E = CPL * 4, G = 32 / LPR;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int grp = lane / LPR, gl = lane % LPR;
@@ -318,31 +372,49 @@ __global__ void __launch_bounds__(256) k_bw(BwArgs a) {
     }
 }
 
-// lowest-index argmin / argmax of each vector of the stored iterate (active rows)
-__global__ void k_bw_argext(const float *S, const int64_t *rp, int64_t n, int32_t stride, int32_t R,
+// lowest-index argmin / argmax of each vector of the stored iterate (active
+// rows); one thread per 16-byte chunk, stride = 1 << sshift
+__global__ void k_bw_argext(const float *S, const int64_t *rp, int64_t n, int32_t sshift, int32_t R,
                             const uint32_t *mn, const uint32_t *mx, unsigned long long *amin, unsigned long long *amax) {
-    const int64_t total = n * R;
+    const int qshift = sshift - 2, qmask = (1 << qshift) - 1;
+    const int64_t total = n << qshift;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / R;
-        const int r = (int)(t - i * R);
-        if (rp[i + 1] == rp[i]) continue;
-        const float v = S[i * stride + r];
-        if (v == ord2f(mn[r])) atomicMin(amin + r, (unsigned long long)i);
-        if (v == ord2f(mx[r])) atomicMin(amax + r, (unsigned long long)i);
+        const int64_t i = t >> qshift;
+        const int q = (int)(t & qmask);
+        if (4 * q >= R || rp[i + 1] == rp[i]) continue;
+        const float4 v4 = __ldg(reinterpret_cast<const float4 *>(S) + t);
+        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int r = 4 * q + e;
+            if (r >= R) break;
+            if (v[e] == ord2f(mn[r])) atomicMin(amin + r, (unsigned long long)i);
+            if (v[e] == ord2f(mx[r])) atomicMin(amax + r, (unsigned long long)i);
+        }
     }
 }
 
-// per-block partial sums of A = sum xbar (x - 1/2), B = sum xbar (x + 1/2), x = a (s - lo) - 1/2
+// per-block partial sums of A = sum xbar (x - 1/2) and B = sum xbar (x + 1/2),
+// x = a (s - lo) - 1/2.  Products in FP32 (FP64 runs on a very narrow pipe on
+// this part), each thread's running sums compensated (Kahan), the threads'
+// sums combined in FP64.  B = A + sum xbar.
 constexpr int kRedBlocks = 304;
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
 __global__ void k_bw_partial(const float *xbar, const float *S, const int64_t *rp, int64_t n, int32_t stride, int32_t R,
                              const uint32_t *mn, const float *a_t, double *partA, double *partB) {
     __shared__ double sA[256], sB[256];
-    // thread layout: r = threadIdx.x % R' (R' = min(R, 256)); rows strided
+    // thread layout: r = threadIdx.x % R, rows strided over the block's R-wide slices
     const int Rp = R;
     const int lanes_per = blockDim.x / Rp > 0 ? blockDim.x / Rp : 1;
     const int r = threadIdx.x % Rp;
     const int sub = threadIdx.x / Rp;
-    double accA = 0.0, accB = 0.0;
+    float accA = 0.f, cA = 0.f, accX = 0.f, cX = 0.f;
     if (sub < lanes_per && threadIdx.x < lanes_per * Rp) {
         const float lo = ord2f(mn[r]);
         const float ar = a_t[r];
@@ -350,18 +422,18 @@ __global__ void k_bw_partial(const float *xbar, const float *S, const int64_t *r
             if (rp[i + 1] == rp[i]) continue;
             const float xb = xbar[i * stride + r];
             const float xv = ar * (S[i * stride + r] - lo) - 0.5f;
-            accA += (double)xb * ((double)xv - 0.5);
-            accB += (double)xb * ((double)xv + 0.5);
+            kahan_add(accA, cA, xb * (xv - 0.5f));
+            kahan_add(accX, cX, xb);
         }
     }
-    sA[threadIdx.x] = accA;
-    sB[threadIdx.x] = accB;
+    sA[threadIdx.x] = (double)accA - (double)cA;
+    sB[threadIdx.x] = (double)accX - (double)cX;
     __syncthreads();
     if (threadIdx.x < Rp) {
-        double tA = 0.0, tB = 0.0;
-        for (int s = 0; s < lanes_per; ++s) { tA += sA[s * Rp + threadIdx.x]; tB += sB[s * Rp + threadIdx.x]; }
+        double tA = 0.0, tX = 0.0;
+        for (int s2 = 0; s2 < lanes_per; ++s2) { tA += sA[s2 * Rp + threadIdx.x]; tX += sB[s2 * Rp + threadIdx.x]; }
         partA[(int64_t)blockIdx.x * Rp + threadIdx.x] = tA;
-        partB[(int64_t)blockIdx.x * Rp + threadIdx.x] = tB;
+        partB[(int64_t)blockIdx.x * Rp + threadIdx.x] = tA + tX;
     }
 }
 
@@ -374,20 +446,31 @@ __global__ void k_bw_reduce(const double *partA, const double *partB, int nblock
     B[r] = tB;
 }
 
-// ybar = a xbar (+ a A at the argmin, - a B at the argmax); U = D^-1 ybar
-__global__ void k_bw_ybar(const float *xbar, const int64_t *rp, const float *Dinv, int64_t n, int32_t stride, int32_t R,
+// ybar = a xbar (+ a A at the argmin, - a B at the argmax); U = D^-1 ybar.
+// a * xbar in FP32 is the correctly rounded product, i.e. what FP64 then
+// rounding gives; FP64 only at the two corrected entries of each vector.
+__global__ void k_bw_ybar(const float *xbar, const int64_t *rp, const float *Dinv, int64_t n, int32_t sshift, int32_t R,
                           const float *a_t, const double *A, const double *B, const unsigned long long *amin,
                           const unsigned long long *amax, float *ybar, float *U) {
-    const int64_t total = n * stride;
+    const int64_t total = n << sshift;
+    const int rmask = (1 << sshift) - 1;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / stride;
-        const int r = (int)(t - i * stride);
+        const int64_t i = t >> sshift;
+        const int r = (int)(t & rmask);
         float yb = 0.f;
-        if (r < R && rp[i + 1] > rp[i] && a_t[r] > 0.f) {
-            double v = (double)a_t[r] * xbar[t];
-            if ((unsigned long long)i == amin[r]) v += (double)a_t[r] * A[r];
-            if ((unsigned long long)i == amax[r]) v -= (double)a_t[r] * B[r];
-            yb = (float)v;
+        if (r < R && rp[i + 1] > rp[i]) {
+            const float ar = __ldg(a_t + r);
+            if (ar > 0.f) {
+                const bool lo_i = (unsigned long long)i == amin[r], hi_i = (unsigned long long)i == amax[r];
+                if (lo_i || hi_i) {
+                    double v = (double)ar * xbar[t];
+                    if (lo_i) v += (double)ar * A[r];
+                    if (hi_i) v -= (double)ar * B[r];
+                    yb = (float)v;
+                } else {
+                    yb = ar * xbar[t];
+                }
+            }
         }
         ybar[t] = yb;
         U[t] = yb * Dinv[i];
@@ -462,7 +545,8 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
     // buffers
     std::vector<float *> seg(c + 1, nullptr);
     for (int u = 1; u <= c; ++u) AD_TRY(dalloc_t(g, (n + 1) * stride, &seg[u]));
-    float *xbar = nullptr, *xbar2 = nullptr, *ybar = nullptr, *U = nullptr, *part = nullptr, *a_t = nullptr;
+    float *xbar = nullptr, *xbar2 = nullptr, *ybar = nullptr, *U = nullptr, *part = nullptr;
+    float *a_t = nullptr, *a_p = nullptr, *a_k = nullptr;   // scales of sweep t, t - 1 and k
     double *G = nullptr, *C = nullptr, *partA = nullptr, *partB = nullptr, *A = nullptr, *B = nullptr;
     unsigned long long *amin = nullptr, *amax = nullptr;
     uint32_t *scratch_mm = nullptr;
@@ -480,10 +564,14 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
     AD_TRY(dalloc_t(g, stride, &amin));
     AD_TRY(dalloc_t(g, stride, &amax));
     AD_TRY(dalloc_t(g, stride, &a_t));
+    AD_TRY(dalloc_t(g, stride, &a_p));
+    AD_TRY(dalloc_t(g, stride, &a_k));
     AD_TRY(dalloc_t(g, 2 * stride, &scratch_mm));
     AD_CUDA_TRY(cudaMemsetAsync(G, 0, (nnz + 1) * sizeof(double), g->stream));
     AD_CUDA_TRY(cudaMemsetAsync(C, 0, (n + 1) * sizeof(double), g->stream));
     const uint32_t *mm_min = sv->mm, *mm_max = sv->mm + (size_t)k * stride;
+    int sshift = 0;   // stride = 1 << sshift (a power of two, at least 4)
+    while ((1 << sshift) < stride) ++sshift;
     auto slot_min = [&](int t) { return mm_min + (size_t)(t - 1) * stride; };   // min/max of s_t, t >= 1
     auto slot_max = [&](int t) { return mm_max + (size_t)(t - 1) * stride; };
 
@@ -494,7 +582,6 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
     a.rho = sv->rho; a.rhobar = rhobar_dev;
     a.G = G; a.C = C; a.part = part;
     fill_bw_plan(a, *plan);
-    std::vector<float> host_scale(stride);
 
     const int nseg = k > 0 ? (k + c - 1) / c : 0;
     if (k == 0) {
@@ -514,9 +601,8 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
                               t >= 2 ? slot_max(t - 1) : nullptr, scratch_mm, scratch_mm + stride));
         }
         if (!have_xbar) {   // distance backward on s_k
-            AD_LAUNCH(k_scale_from_mm, 1, 256, 0, g->stream, slot_min(k), slot_max(k), stride, a_t);
-            AD_TRY(copy_out(g, host_scale.data(), a_t, stride * sizeof(float)));
-            for (int r = 0; r < stride && r < 256; ++r) a.a_k[r] = r < R ? host_scale[r] : 0.f;
+            AD_LAUNCH(k_scale_from_mm, 1, 256, 0, g->stream, slot_min(k), slot_max(k), stride, a_k);
+            a.a_k = a_k;
             a.mode = 0;
             a.Sk = seg[len];
             a.xbar_out = xbar;
@@ -530,20 +616,19 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
             AD_LAUNCH(k_scale_from_mm, 1, 256, 0, g->stream, slot_min(t), slot_max(t), stride, a_t);
             AD_CUDA_TRY(cudaMemsetAsync(amin, 0xff, stride * sizeof(unsigned long long), g->stream));
             AD_CUDA_TRY(cudaMemsetAsync(amax, 0xff, stride * sizeof(unsigned long long), g->stream));
-            AD_LAUNCH(k_bw_argext, g->num_sms * 16, 256, 0, g->stream, St, g->rp, n, stride, R, slot_min(t), slot_max(t),
-                      amin, amax);
+            AD_LAUNCH(k_bw_argext, g->num_sms * 16, 256, 0, g->stream, St, g->rp, n, sshift, R, slot_min(t),
+                      slot_max(t), amin, amax);
             AD_LAUNCH(k_bw_partial, kRedBlocks, 256, 0, g->stream, xbar, St, g->rp, n, stride, R, slot_min(t), a_t, partA,
                       partB);
             AD_LAUNCH(k_bw_reduce, 1, 256, 0, g->stream, partA, partB, kRedBlocks, R, A, B);
-            AD_LAUNCH(k_bw_ybar, g->num_sms * 16, 256, 0, g->stream, xbar, g->rp, g->Dinv, n, stride, R, a_t, A, B, amin,
+            AD_LAUNCH(k_bw_ybar, g->num_sms * 16, 256, 0, g->stream, xbar, g->rp, g->Dinv, n, sshift, R, a_t, A, B, amin,
                       amax, ybar, U);
             // sweep adjoint + weight terms
             if (t >= 2) {
-                AD_LAUNCH(k_scale_from_mm, 1, 256, 0, g->stream, slot_min(t - 1), slot_max(t - 1), stride, a_t);
-                AD_TRY(copy_out(g, host_scale.data(), a_t, stride * sizeof(float)));
-                for (int r = 0; r < stride && r < 256; ++r) a.a_prev[r] = host_scale[r];
+                AD_LAUNCH(k_scale_from_mm, 1, 256, 0, g->stream, slot_min(t - 1), slot_max(t - 1), stride, a_p);
+                a.a_prev = a_p;
             } else {
-                for (int r = 0; r < 256; ++r) a.a_prev[r] = 1.f;
+                a.a_prev = nullptr;
             }
             a.mode = 1;
             a.U = U;
@@ -559,7 +644,7 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
     AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
     for (int u = 1; u <= c; ++u) dfree(g, seg[u]);
     for (void *p : {(void *)xbar, (void *)xbar2, (void *)ybar, (void *)U, (void *)part, (void *)G, (void *)C,
-                    (void *)partA, (void *)partB, (void *)A, (void *)B, (void *)amin, (void *)amax, (void *)a_t,
+                    (void *)partA, (void *)partB, (void *)A, (void *)B, (void *)amin, (void *)amax, (void *)a_t, (void *)a_p, (void *)a_k,
                     (void *)scratch_mm})
         dfree(g, p);
     return AD_OK;

@@ -245,7 +245,7 @@ __device__ __forceinline__ void put_ranks(const RankOut &o, int64_t p, int d, ui
     o.desc[p] = (uint32_t)d - leq + (r_asc - lt);
 }
 
-constexpr int kSortCap = 2048;      // rows up to this degree are sorted by one CTA
+constexpr int kSortCap = 4096;      // rows up to this degree are sorted by one CTA (32 KB of shared memory)
 
 // rows of degree <= GS (8 or 32): a group of GS lanes per row, one entry per
 // lane, rank = number of smaller (key, position) pairs in the row
@@ -387,7 +387,7 @@ __device__ void block_bitonic(unsigned long long *a, int len_pow2) {
     }
 }
 
-// rows of degree in (128, kSortCap]: a CTA per row, bitonic sort of (key, position)
+// rows of degree in (512, kSortCap]: a CTA per row, bitonic sort of (key, position)
 __device__ __forceinline__ int lower_bound_smem(const unsigned long long *a, int n, unsigned long long v) {
     int lo = 0, hi = n;
     while (lo < hi) {

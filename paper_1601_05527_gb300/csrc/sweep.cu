@@ -25,7 +25,7 @@ static Config pick_config(int R, ad_storage storage) {
     c.nchunks = (R + c.V - 1) / c.V;
     int p2 = 1;
     while (p2 < c.nchunks) p2 <<= 1;
-    c.lpr = p2 < 32 ? p2 : 32;
+    c.lpr = p2 < AD_MAX_LPR ? p2 : AD_MAX_LPR;
     c.cpl = p2 / c.lpr;
     c.stride = p2 * c.V;
     return c;
@@ -95,6 +95,8 @@ ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, 
     a.omega = (float)omega;
     a.voff = g->voff; a.G = g->G; a.blocked = g->G > 1 ? 1 : 0;
     a.anchor = g->anchor;
+    AD_TRY(ensure(g, g->ac, (size_t)g->G * 2 * cf.stride * sizeof(float)));
+    a.ac = static_cast<float *>(g->ac.ptr);
     fill_plan(a, *sp);
     a.x_in = x_in; a.x_out = x_out;
     a.mm_prev_min = pmin; a.mm_prev_max = pmax; a.mm_min = mn; a.mm_max = mx;
@@ -149,6 +151,8 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
     a.G = g->G;
     a.blocked = g->G > 1 ? 1 : 0;
     a.anchor = g->anchor;
+    AD_TRY(ensure(g, g->ac, (size_t)g->G * 2 * cf.stride * sizeof(float)));
+    a.ac = static_cast<float *>(g->ac.ptr);
 
     void *xin = g->x0.ptr, *xout = g->x1.ptr;
     const size_t smem = 2 * 8 * (size_t)cf.stride * sizeof(float);

@@ -32,6 +32,9 @@
 #ifndef AD_SWEEP_MINB
 #define AD_SWEEP_MINB 4        // minimum resident CTAs per SM requested from ptxas
 #endif
+#ifndef AD_MAX_LPR
+#define AD_MAX_LPR 32          // most lanes that share one row (more chunks go to each lane beyond it)
+#endif
 #ifndef AD_COL_STREAM
 #define AD_COL_STREAM 1        // 1: read column indices with the streaming (evict-first) hint
 #endif
@@ -78,6 +81,7 @@ struct SweepArgs {
     int32_t G;
     int32_t blocked;
     const int32_t *anchor;   // [G] vertex whose previous value is subtracted (the stored frame's centre)
+    float *ac;               // [G][2][stride]: scale a and centre c of this sweep (k_scale_center)
 };
 
 __device__ __forceinline__ int graph_of(const int64_t *voff, int G, int64_t row) {
@@ -158,7 +162,8 @@ __device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int6
     using L = Lane<T, LPR, CPL>;
     constexpr int V = L::V, G = L::G;
     constexpr int U = 32 / G;                       // neighbours per group per batch of 32
-    constexpr int UB = (AD_SWEEP_UB / CPL) < U ? (AD_SWEEP_UB / CPL) : U;   // loads in flight per chunk slot
+    constexpr int UBc = AD_SWEEP_UB / CPL > 0 ? AD_SWEEP_UB / CPL : 1;
+    constexpr int UB = UBc < U ? UBc : U;          // loads in flight per chunk slot
     const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
     const int64_t row_q = a.stride / V;   // 16-byte chunks per row
     for (int64_t base = p0; base < p1; base += 32) {
@@ -261,9 +266,7 @@ __device__ __forceinline__ void load_own(const SweepArgs &a, int64_t row, int gl
 
 template <typename T, int LPR, int CPL>
 __device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, int gl, const uint4 (&own)[CPL],
-                                             const float (&S)[CPL * Store<T>::V],
-                                             const float (&A)[CPL * Store<T>::V],
-                                             const float (&C)[CPL * Store<T>::V],
+                                             const float (&S)[CPL * Store<T>::V], const float *acg,
                                              float (&mn)[CPL * Store<T>::V], float (&mx)[CPL * Store<T>::V]) {
     constexpr int V = Store<T>::V;
     uint4 *Y = reinterpret_cast<uint4 *>(a.x_out);
@@ -274,12 +277,19 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, in
     for (int c = 0; c < CPL; ++c) {
         const int q = gl + c * LPR;
         if (q < a.nchunks) {
-            float y[V], o[V];
+            float y[V], o[V], A[V], C[V];
             Store<T>::unpack(own[c], y);
+#pragma unroll
+            for (int e4 = 0; e4 < V / 4; ++e4) {   // scale and centre of the row's graph (the same line for every row)
+                const float4 av = __ldg(reinterpret_cast<const float4 *>(acg + q * V) + e4);
+                const float4 cv = __ldg(reinterpret_cast<const float4 *>(acg + a.stride + q * V) + e4);
+                A[4 * e4] = av.x; A[4 * e4 + 1] = av.y; A[4 * e4 + 2] = av.z; A[4 * e4 + 3] = av.w;
+                C[4 * e4] = cv.x; C[4 * e4 + 1] = cv.y; C[4 * e4 + 2] = cv.z; C[4 * e4 + 3] = cv.w;
+            }
 #pragma unroll
             for (int e = 0; e < V; ++e) {
                 const float z = fmaf(om1, y[e], om * (S[c * V + e] * dinv));
-                o[e] = Store<T>::round(A[c * V + e] * (z - C[c * V + e]));
+                o[e] = Store<T>::round(A[e] * (z - C[e]));
                 mn[c * V + e] = fminf(mn[c * V + e], o[e]);
                 mx[c * V + e] = fmaxf(mx[c * V + e], o[e]);
             }
@@ -309,20 +319,31 @@ __device__ __forceinline__ void load_scale(const uint32_t *pmin, const uint32_t 
         }
 }
 
-// Centre c of the stored frame: the previous values of the graph's anchor vertex.
-template <typename T, int LPR, int CPL>
-__device__ __forceinline__ void load_center(const SweepArgs &a, int g, int gl, float (&C)[CPL * Store<T>::V]) {
+// Scale a = 1 / (max - min) of the previous sweep's stored values (1 before the
+// first sweep, 0 for a vector with max == min) and centre c of the stored frame
+// (the previous values of the graph's anchor vertex), once per graph and sweep,
+// so that the sweep reads them from one cached line instead of holding them in
+// registers.  Block g, one thread per 16-byte chunk.
+template <typename T>
+__global__ void k_scale_center(const uint32_t *pmin, const uint32_t *pmax, const void *x_in, const int32_t *anchor,
+                               int32_t stride, float *ac) {
     constexpr int V = Store<T>::V;
-    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
-    const int64_t row = a.anchor[g];
-    const int64_t row_q = a.stride / V;
+    const int g = blockIdx.x;
+    float *A = ac + (size_t)g * 2 * stride, *C = A + stride;
+    const uint4 *xa = reinterpret_cast<const uint4 *>(x_in) + (int64_t)anchor[g] * (stride / V);
+    for (int q = threadIdx.x; q < stride / V; q += blockDim.x) {
+        float f[V];
+        Store<T>::unpack(xa[q], f);
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-        const int q = gl + c * LPR;
-        if (q < a.nchunks) Store<T>::unpack(__ldg(X + row * row_q + q), C + c * V);
-        else {
-#pragma unroll
-            for (int e = 0; e < V; ++e) C[c * V + e] = 0.f;
+        for (int e = 0; e < V; ++e) {
+            const int r = q * V + e;
+            float av = 1.f;
+            if (pmin) {   // FP32 on purpose: FP64 division runs on a very narrow pipe on this part
+                const float lo = ord2f(pmin[(size_t)g * stride + r]), hi = ord2f(pmax[(size_t)g * stride + r]);
+                av = hi > lo ? 1.f / (hi - lo) : 0.f;
+            }
+            A[r] = av;
+            C[r] = f[e];
         }
     }
 }
@@ -334,8 +355,9 @@ __device__ __forceinline__ void load_center(const SweepArgs &a, int g, int gl, f
 template <typename T, int LPR, int CPL>
 struct LaneStats {
     static constexpr int V = Store<T>::V, E = CPL * V;
-    float A[E], C[E], mn[E], mx[E];
+    float mn[E], mx[E];
     int cg = -1;
+    const float *acg = nullptr;   // scale and centre of graph cg
 
     __device__ __forceinline__ void flush(const SweepArgs &a, int gl) {
         if (cg < 0) return;
@@ -350,14 +372,12 @@ struct LaneStats {
                 }
             }
     }
-    // make the lane's state describe graph `g` (scale and centre from its previous sweep)
+    // make the lane's state describe graph `g`
     __device__ __forceinline__ void enter(const SweepArgs &a, int gl, int g, bool flush_old) {
         if (g == cg) return;
         if (flush_old) flush(a, gl);
         cg = g;
-        load_scale<T, LPR, CPL>(a.mm_prev_min ? a.mm_prev_min + (size_t)g * a.stride : nullptr,
-                                a.mm_prev_max ? a.mm_prev_max + (size_t)g * a.stride : nullptr, gl, A);
-        load_center<T, LPR, CPL>(a, g, gl, C);
+        acg = a.ac + (size_t)g * 2 * a.stride;
 #pragma unroll
         for (int e = 0; e < E; ++e) { mn[e] = INFINITY; mx[e] = -INFINITY; }
     }
@@ -438,7 +458,7 @@ __global__ void __launch_bounds__(256, AD_SWEEP_MINB) k_sweep(SweepArgs a) {
                 reduce_groups<LPR, E>(S);
                 if (grp == 0) {
                     ls.enter(a, gl, row_graph(row), true);
-                    row_epilogue<T, LPR, CPL>(a, row, gl, own, S, ls.A, ls.C, ls.mn, ls.mx);
+                    row_epilogue<T, LPR, CPL>(a, row, gl, own, S, ls.acg, ls.mn, ls.mx);
                 }
                 if (lane == 0) a.big_counter[t0] = 0u;
             }
@@ -451,7 +471,7 @@ __global__ void __launch_bounds__(256, AD_SWEEP_MINB) k_sweep(SweepArgs a) {
             reduce_groups<LPR, E>(acc);
             if (grp == 0) {
                 ls.enter(a, gl, row_graph(row), true);
-                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.A, ls.C, ls.mn, ls.mx);
+                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.acg, ls.mn, ls.mx);
             }
         } else {
             // ---- G low-degree rows, one per lane group
@@ -462,7 +482,7 @@ __global__ void __launch_bounds__(256, AD_SWEEP_MINB) k_sweep(SweepArgs a) {
                 load_own<T, LPR, CPL>(a, row, gl, own);
                 group_gather<T, LPR, CPL>(a, a.rp[row], a.rp[row + 1], gl, acc);
                 ls.enter(a, gl, row_graph(row), true);
-                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.A, ls.C, ls.mn, ls.mx);
+                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.acg, ls.mn, ls.mx);
             }
         }
     }
@@ -522,11 +542,41 @@ __global__ void __launch_bounds__(256, AD_SWEEP_MINB) k_sweep(SweepArgs a) {
 // eoff[i] + (p - upos[i]), rho_e = sqrt(sum_r a_r^2 (y_i^r - y_j^r)^2).
 // A lane group handles one edge; its lanes hold different chunks of R.
 // ----------------------------------------------------------------------------
+// Sums of K values over the LPR lanes of a group, transposed: each exchange
+// halves the values a lane holds, so K sums take about LPR shuffles in total
+// instead of K * log2(LPR).  Afterwards lane gl holds in s[0 .. NH) the sums of
+// values which .. which + NH - 1 (NH = max(1, K / LPR)); when LPR > K the lanes
+// that differ only in their low bits hold the same sums.
+template <int LPR, int K>
+__device__ __forceinline__ void group_sums(float (&s)[K], int gl, unsigned gmask, int &which) {
+    static_assert(K >= 1 && (K & (K - 1)) == 0, "the transposed sums halve K: K must be a power of two");
+    which = 0;
+#pragma unroll
+    for (int o = LPR / 2, c = K; o >= 1; o >>= 1) {
+        if (c > 1) {
+            const bool upper = (gl & o) != 0;
+#pragma unroll
+            for (int i = 0; i < K / 2; ++i) {
+                if (i < c / 2) {
+                    const float send = upper ? s[i] : s[i + c / 2];
+                    const float keep = upper ? s[i + c / 2] : s[i];
+                    s[i] = keep + __shfl_xor_sync(gmask, send, o);
+                }
+            }
+            if (upper) which += c / 2;
+            c >>= 1;
+        } else {
+            s[0] += __shfl_xor_sync(gmask, s[0], o);
+        }
+    }
+}
+
 template <typename T, int LPR, int CPL>
 __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64_t p0, int64_t p1, int step,
                                           int first, int gl, unsigned gmask, const float (&A2)[CPL * Store<T>::V]) {
     constexpr int V = Store<T>::V, E = CPL * V;
-    constexpr int UB = AD_SWEEP_UB;     // edges of one group in flight
+    // edges of one group in flight: the largest power of two <= AD_SWEEP_UB (group_sums halves it)
+    constexpr int UB = AD_SWEEP_UB >= 8 ? 8 : AD_SWEEP_UB >= 4 ? 4 : AD_SWEEP_UB >= 2 ? 2 : 1;
     const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
     const int64_t row_q = a.stride / V;
     float yi[E];
@@ -573,30 +623,9 @@ __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64
                 }
             }
         }
-        // sums over the group's lanes, transposed: each exchange halves the
-        // values a lane holds, so UB sums take about LPR shuffles in total
-        // instead of UB * log2(LPR); afterwards lane gl holds the sums of
-        // edges which .. which + NH - 1
-        constexpr int NH = UB / LPR > 0 ? UB / LPR : 1;
         int which = 0;
-#pragma unroll
-        for (int o = LPR / 2, c = UB; o >= 1; o >>= 1) {
-            if (c > 1) {
-                const bool upper = (gl & o) != 0;
-#pragma unroll
-                for (int i = 0; i < UB / 2; ++i) {
-                    if (i < c / 2) {
-                        const float send = upper ? s[i] : s[i + c / 2];
-                        const float keep = upper ? s[i + c / 2] : s[i];
-                        s[i] = keep + __shfl_xor_sync(gmask, send, o);
-                    }
-                }
-                if (upper) which += c / 2;
-                c >>= 1;
-            } else {
-                s[0] += __shfl_xor_sync(gmask, s[0], o);
-            }
-        }
+        group_sums<LPR, UB>(s, gl, gmask, which);
+        constexpr int NH = UB / LPR > 0 ? UB / LPR : 1;
         const bool writer = (LPR <= UB) || (gl % (LPR / UB) == 0);
 #pragma unroll
         for (int i = 0; i < NH; ++i) {
@@ -669,6 +698,8 @@ struct Config {
 
 template <typename T, int LPR, int CPL>
 ad_status launch_sweep(ad_graph_t g, const SweepArgs &a, int blocks, size_t smem) {
+    AD_LAUNCH(k_scale_center<T>, a.G, 32, 0, g->stream, a.mm_prev_min, a.mm_prev_max, a.x_in, a.anchor, a.stride,
+              a.ac);
     AD_LAUNCH((k_sweep<T, LPR, CPL>), blocks, 256, smem, g->stream, a);
     return AD_OK;
 }
@@ -709,6 +740,13 @@ ad_status dispatch(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &
         case 1601: return run(integral_constant<int, 16>{}, integral_constant<int, 1>{});
         case 3201: return run(integral_constant<int, 32>{}, integral_constant<int, 1>{});
         case 3202: return run(integral_constant<int, 32>{}, integral_constant<int, 2>{});
+#if AD_MAX_LPR < 32
+        case 202: return run(integral_constant<int, 2>{}, integral_constant<int, 2>{});
+        case 204: return run(integral_constant<int, 2>{}, integral_constant<int, 4>{});
+        case 402: return run(integral_constant<int, 4>{}, integral_constant<int, 2>{});
+        case 404: return run(integral_constant<int, 4>{}, integral_constant<int, 4>{});
+        case 802: return run(integral_constant<int, 8>{}, integral_constant<int, 2>{});
+#endif
         default: return fail(AD_ERR_INVALID_ARG, "unsupported R / storage combination");
     }
 }

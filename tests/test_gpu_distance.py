@@ -187,3 +187,37 @@ def test_full_size_rmat20_parity_two_sweeps():
     rho = gpu_rho(g, 32, 2, 0.5, seed=0x1601055270000000)
     ref = ref_rho(g, 32, 2, 0.5, seed=0x1601055270000000)
     assert_rho_close(rho, ref)
+
+
+def test_repeated_calls_replay_the_same_results():
+    """On a handle bound to a capturable stream the second identical call is
+    recorded as a CUDA graph and later ones replay it: every call must give
+    the same distances, and a change of seed, storage or edge weights must be
+    seen by the next call."""
+    import torch
+    L = lib()
+    base = graphgen.rmat(11, 8, seed=4)
+    g = graphgen.with_edge_weights(base, graphgen.uniform_edge_weights(base.m, seed=5))
+    s = torch.cuda.Stream()
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, g.weight, 0, s)
+    w64 = g.weight.astype(np.float64)
+    ref = oracle.algebraic_distance(g.row_ptr, g.col, w64, R=16, k=12, omega=0.5, seed=3)
+    outs = []
+    for _ in range(4):
+        rho = np.zeros(g.m, np.float32)
+        L.ad_algebraic_distance(h, 16, 12, 0.5, 3, 0, "fp32", 0, rho)
+        outs.append(rho)
+    for r in outs:
+        np.testing.assert_array_equal(r, outs[0])
+    assert_rho_close(outs[0], ref)
+    rho = np.zeros(g.m, np.float32)
+    L.ad_algebraic_distance(h, 16, 12, 0.5, 4, 0, "fp32", 0, rho)          # new seed
+    assert_rho_close(rho, oracle.algebraic_distance(g.row_ptr, g.col, w64, R=16, k=12, omega=0.5, seed=4))
+    new_w = graphgen.uniform_edge_weights(g.m, seed=9)
+    L.ad_graph_set_edge_weights(h, new_w)
+    g2 = graphgen.with_edge_weights(g, new_w)
+    for _ in range(3):                                                       # same call, new weights
+        L.ad_algebraic_distance(h, 16, 12, 0.5, 4, 0, "fp32", 0, rho)
+    assert_rho_close(rho, oracle.algebraic_distance(g2.row_ptr, g2.col, g2.weight.astype(np.float64), R=16, k=12,
+                                                    omega=0.5, seed=4))
+    L.ad_graph_destroy(h)

@@ -17,8 +17,20 @@ SEL_GRAPHS = {
     "rmat12": lambda: graphgen.rmat(12, 16, seed=3),
     "ba2000": lambda: graphgen.barabasi_albert(2000, 6, seed=2),
     "grid32": lambda: graphgen.grid2d(32, 32),
-    "rmat14": lambda: graphgen.rmat(14, 16, seed=5),       # rows of degree > 2048 (chunked ranks)
+    "rmat14": lambda: graphgen.rmat(14, 16, seed=5),
+    "hubs": lambda: hub_graph(),                           # rows of degree > 4096 (radix-sorted ranks)
 }
+
+
+def hub_graph(n=30000, seed=6):
+    """Sparse random graph plus four hubs of degree 4500..9000."""
+    rng = np.random.default_rng(seed)
+    u = [rng.integers(0, n, 60000)]
+    v = [rng.integers(0, n, 60000)]
+    for h, d in zip(range(4), (4500, 6000, 7500, 9000)):
+        u.append(np.full(d, h))
+        v.append(rng.choice(np.arange(4, n), d, replace=False))
+    return graphgen.from_edges(n, np.concatenate(u), np.concatenate(v))
 
 
 def gpu_select(g, scores, fraction, mode, scope):
