@@ -68,6 +68,9 @@ def _L():
                 "orc_target_count": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_double]),
                 "orc_sparsify": (ctypes.c_int, [ctypes.c_int64, I64P, I32P, F64P, ctypes.c_int32, ctypes.c_int32,
                                                 ctypes.c_double, U8P, I64P, F64P]),
+                "orc_binned_ranks": (ctypes.c_int, [ctypes.c_int64, I64P, I32P, F64P, ctypes.c_uint64, I64P, I64P]),
+                "orc_sparsify_binned": (ctypes.c_int, [ctypes.c_int64, I64P, I32P, F64P, ctypes.c_uint64,
+                                                       ctypes.c_double, U8P, I64P, F64P]),
                 "orc_create_seeds": (ctypes.c_int, [ctypes.c_int64, I64P, I32P, F64P, ctypes.c_double, U8P]),
                 "orc_aggregate": (ctypes.c_int64, [ctypes.c_int64, I64P, I32P, F64P, U8P, I32P]),
                 "orc_galerkin": (ctypes.c_int64, [ctypes.c_int64, I64P, I32P, F64P, I32P, ctypes.c_int64,
@@ -214,6 +217,33 @@ def sparsify(rp, ci, score, mode, scope, fraction):
                            fraction, _p(keep, U8P), ctypes.byref(nk), ctypes.byref(eu))
     if st != 0:
         raise RuntimeError(f"oracle sparsify failed ({st})")
+    return keep, nk.value, eu.value
+
+
+def binned_ranks(rp, ci, score, seed, return_bins=False):
+    """Selection rank of every CSR entry under SparsifyB (Alg. 3, reading R13);
+    with return_bins also the bin of every entry."""
+    rp, ci, _ = _csr(rp, ci)
+    s = np.ascontiguousarray(score, dtype=np.float64)
+    rank = np.zeros(int(rp[-1]), dtype=np.int64)
+    bins = np.zeros(int(rp[-1]), dtype=np.int64)
+    if _L().orc_binned_ranks(len(rp) - 1, _p(rp, I64P), _p(ci, I32P), _p(s, F64P), int(seed) & (2**64 - 1),
+                             _p(rank, I64P), _p(bins, I64P)) != 0:
+        raise RuntimeError("oracle binned ranks failed")
+    return (rank, bins) if return_bins else rank
+
+
+def sparsify_binned(rp, ci, score, seed, fraction):
+    """SparsifyB to a target fraction: (keep[m] uint8, n_kept, e_used)."""
+    rp, ci, _ = _csr(rp, ci)
+    s = np.ascontiguousarray(score, dtype=np.float64)
+    keep = np.zeros(len(s), dtype=np.uint8)
+    nk = ctypes.c_int64(0)
+    eu = ctypes.c_double(0)
+    st = _L().orc_sparsify_binned(len(rp) - 1, _p(rp, I64P), _p(ci, I32P), _p(s, F64P), int(seed) & (2**64 - 1),
+                                  fraction, _p(keep, U8P), ctypes.byref(nk), ctypes.byref(eu))
+    if st != 0:
+        raise RuntimeError(f"oracle binned sparsify failed ({st})")
     return keep, nk.value, eu.value
 
 

@@ -57,6 +57,19 @@
  *       is the fraction of that level's current edges to keep, met by fitting
  *       e with the bisection of R8.  Philox stream of level l is 2l on
  *       the way down and 2l+1 for the recomputation on the way up.
+ *   R13 SparsifyB (Alg. 3; its text stops mid-sentence).  Per node, sigma is
+ *       the population standard deviation of its incident distances; the bin
+ *       width is h = 3.5 sigma / cbrt(d) and the bin of a distance is
+ *       floor((rho - min) / h) (one bin when sigma = 0).  "Randomly select
+ *       bins and edges up to d^e" is read as a stratified draw: entries of a
+ *       bin in random order, bins in random order, then round robin over the
+ *       bins until T(d, e) entries are taken (reading R7), so every bin
+ *       contributes before any contributes twice.  Random order = ascending
+ *       word 0 of Philox4x32-10 with key = the selection seed and counter
+ *       (edge id lo, hi, 0, 0xB1000000) for an entry, (vertex lo, hi, 1 + bin,
+ *       0xB1000000) for a bin; ties by position / bin index.  Sums for mean
+ *       and sigma run sequentially in CSR order.  Union over the two ends of
+ *       an edge and the fit of e are those of Alg. 2 (R8).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -376,6 +389,153 @@ int orc_sparsify(int64_t n, const int64_t *rp, const int32_t *ci, const double *
     *n_kept = union_of_tops(n, rp, sorted_e, m, hi, keep);
     *e_used = hi;
     free(sorted_e);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 3 (SparsifyB): per node, the incident distances are put into bins    */
+/* whose width follows the rule quoted in Sec. 4, h = 3.5 sigma / d^(1/3),   */
+/* and edges are drawn from all bins (reading R13).                          */
+/* ------------------------------------------------------------------------ */
+#define ORC_BIN_STREAM 0xB1000000u
+
+static uint32_t bin_word(uint64_t seed, uint64_t a, uint32_t z)
+{
+    const uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), z, ORC_BIN_STREAM};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+typedef struct { int64_t bin; uint32_t u; int64_t t; } binned_entry;
+
+static int cmp_binned(const void *a, const void *b)
+{
+    const binned_entry *x = (const binned_entry *)a, *y = (const binned_entry *)b;
+    if (x->bin != y->bin) return x->bin < y->bin ? -1 : 1;
+    if (x->u != y->u) return x->u < y->u ? -1 : 1;
+    return (x->t < y->t) ? -1 : (x->t > y->t);
+}
+
+typedef struct { uint32_t v; int64_t bin; } bin_key;
+
+static int cmp_bin_key(const void *a, const void *b)
+{
+    const bin_key *x = (const bin_key *)a, *y = (const bin_key *)b;
+    if (x->v != y->v) return x->v < y->v ? -1 : 1;
+    return (x->bin < y->bin) ? -1 : (x->bin > y->bin);
+}
+
+/*
+ * Selection rank of every CSR entry under SparsifyB; node i keeps its entries
+ * of rank < T(d_i, e).  For row i with distances rho_1..rho_d (CSR order):
+ *   mean and sigma (population) by sequential FP64 sums in CSR order;
+ *   sigma == 0: one bin; else h = 3.5 sigma / cbrt(d), bin = floor((rho - min) / h);
+ *   entries of a bin in order of (Philox word of the edge id, position);
+ *   bins in order of (Philox word of (i, 1 + bin), bin);
+ *   selection order = round robin over the bins: round r takes the r-th entry
+ *   of every bin that has one, bins in their order.
+ * bin (nullable) receives the bin of every CSR entry.  Returns ORC_OK or ORC_ERR_OOM.
+ */
+int orc_binned_ranks(int64_t n, const int64_t *rp, const int32_t *ci, const double *score, uint64_t seed,
+                     int64_t *rank, int64_t *bin)
+{
+    int64_t nnz = rp[n];
+    int64_t *eid = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t maxd = 0;
+    for (int64_t i = 0; i < n; ++i) if (rp[i + 1] - rp[i] > maxd) maxd = rp[i + 1] - rp[i];
+    size_t md = (size_t)(maxd > 0 ? maxd : 1);
+    binned_entry *a = (binned_entry *)malloc(sizeof(binned_entry) * md);
+    bin_key *bk = (bin_key *)malloc(sizeof(bin_key) * md);
+    int64_t *size = (int64_t *)malloc(sizeof(int64_t) * md);
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * md);   /* position of a bin in the bin order */
+    int64_t *within = (int64_t *)malloc(sizeof(int64_t) * md);
+    if (!eid || !a || !bk || !size || !order || !within) {
+        free(eid); free(a); free(bk); free(size); free(order); free(within);
+        return ORC_ERR_OOM;
+    }
+    orc_entry_edge_ids(n, rp, ci, eid);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t p0 = rp[i], d = rp[i + 1] - p0;
+        if (d == 0) continue;
+        double sum = 0.0, lo = score[eid[p0]], hi = lo;
+        for (int64_t t = 0; t < d; ++t) {
+            const double x = score[eid[p0 + t]];
+            sum += x;
+            if (x < lo) lo = x;
+            if (x > hi) hi = x;
+        }
+        const double mean = sum / (double)d;
+        double q = 0.0;
+        for (int64_t t = 0; t < d; ++t) {
+            const double dx = score[eid[p0 + t]] - mean;
+            q += dx * dx;
+        }
+        const double sigma = sqrt(q / (double)d);
+        const double h = 3.5 * sigma / cbrt((double)d);
+        int64_t nbins = 1;
+        for (int64_t t = 0; t < d; ++t) {
+            int64_t b = 0;
+            if (sigma > 0.0 && hi > lo) b = (int64_t)floor((score[eid[p0 + t]] - lo) / h);
+            a[t].bin = b;
+            a[t].u = bin_word(seed, (uint64_t)eid[p0 + t], 0u);
+            a[t].t = t;
+            if (b + 1 > nbins) nbins = b + 1;
+        }
+        qsort(a, (size_t)d, sizeof(binned_entry), cmp_binned);
+        for (int64_t b = 0; b < nbins; ++b) size[b] = 0;
+        for (int64_t s = 0; s < d; ++s) {
+            within[s] = size[a[s].bin];
+            size[a[s].bin] += 1;
+        }
+        for (int64_t b = 0; b < nbins; ++b) {
+            bk[b].v = bin_word(seed, (uint64_t)i, (uint32_t)(1 + b));
+            bk[b].bin = b;
+        }
+        qsort(bk, (size_t)nbins, sizeof(bin_key), cmp_bin_key);
+        for (int64_t o = 0; o < nbins; ++o) order[bk[o].bin] = o;
+        for (int64_t s = 0; s < d; ++s) {
+            const int64_t r = within[s], b = a[s].bin;
+            int64_t rk = 0;
+            for (int64_t c = 0; c < nbins; ++c) {
+                rk += size[c] < r ? size[c] : r;                 /* entries of earlier rounds */
+                if (size[c] > r && order[c] < order[b]) ++rk;   /* this round, earlier bins */
+            }
+            rank[p0 + a[s].t] = rk;
+            if (bin) bin[p0 + a[s].t] = b;
+        }
+    }
+    free(eid); free(a); free(bk); free(size); free(order); free(within);
+    return ORC_OK;
+}
+
+/* SparsifyB to a target fraction: e bisected as in orc_sparsify (reading R8). */
+int orc_sparsify_binned(int64_t n, const int64_t *rp, const int32_t *ci, const double *score, uint64_t seed,
+                        double fraction, uint8_t *keep, int64_t *n_kept, double *e_used)
+{
+    if (fraction < 0.0 || fraction > 1.0) return ORC_ERR_ARG;
+    int64_t m = orc_count_edges(n, rp, ci), nnz = rp[n];
+    int64_t K = orc_target_count(m, fraction);
+    int64_t *rank = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t *eid = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t *sorted_e = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!rank || !eid || !sorted_e) { free(rank); free(eid); free(sorted_e); return ORC_ERR_OOM; }
+    if (orc_binned_ranks(n, rp, ci, score, seed, rank, NULL) != ORC_OK) {
+        free(rank); free(eid); free(sorted_e);
+        return ORC_ERR_OOM;
+    }
+    orc_entry_edge_ids(n, rp, ci, eid);
+    for (int64_t i = 0; i < n; ++i)   /* ranks of a row are 0 .. d-1: the row in selection order */
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) sorted_e[rp[i] + rank[p]] = eid[p];
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 40; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (union_of_tops(n, rp, sorted_e, m, mid, keep) >= K) hi = mid; else lo = mid;
+    }
+    *n_kept = union_of_tops(n, rp, sorted_e, m, hi, keep);
+    *e_used = hi;
+    free(rank); free(eid); free(sorted_e);
     return ORC_OK;
 }
 
