@@ -270,6 +270,28 @@ ad_status ad_select_per_node(ad_graph_t g, const float *score, double e, ad_mode
                              int64_t *n_kept);
 
 /*
+ * SparsifyB, the binned ("mixture") single-level sparsification of Alg. 3
+ * (Sec. 4): for every node, the distances of its incident edges are put into
+ * bins of width h = 3.5 sigma / d^(1/3) (sigma: their population standard
+ * deviation; one bin when sigma = 0), and the node takes T(d, e) of its edges
+ * by drawing from all bins in turn -- entries of a bin and the bins themselves
+ * in random order, round robin over the bins -- so that short- and long-range
+ * connections are both kept.  An edge is kept when either end takes it; e is
+ * fitted to reach K = floor(fraction * m + 1/2) edges exactly as in
+ * ad_sparsify's per-node scope.  The random order comes from Philox4x32-10 with
+ * key = seed: word 0 of counter (edge id, 0, 0xB1000000) for an edge and of
+ * (vertex, 1 + bin, 0xB1000000) for a bin of that vertex.
+ *   score     [m] FP32 scores (non-negative, finite), host or device; NULL =
+ *             the distances of the last ad_algebraic_distance call.
+ *   keep_out  [m] uint8, host or device; n_kept, e_used may be NULL.
+ * Errors: AD_ERR_INVALID_ARG (fraction outside [0, 1], bad scores, a row with
+ * 2^24 bins or more), AD_ERR_STATE (score NULL and no distances), AD_ERR_OOM,
+ * AD_ERR_CUDA.
+ */
+ad_status ad_sparsify_binned(ad_graph_t g, const float *score, double fraction, uint64_t seed, uint8_t *keep_out,
+                             int64_t *n_kept, double *e_used);
+
+/*
  * Whole-graph ranking (as ad_sparsify_scores with AD_SCOPE_WHOLE_GRAPH on a
  * single graph whose edge ids are 0..m-1) for callers that cannot let a
  * library allocate device memory -- a process whose device memory is all

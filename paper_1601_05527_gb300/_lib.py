@@ -71,6 +71,7 @@ _SIGS = {
     "ad_sparsify": (ctypes.c_int, [_VP, _D, ctypes.c_int, ctypes.c_int, _VP, _PI64, _PD]),
     "ad_sparsify_scores": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, ctypes.c_int, _VP, _PI64, _PD]),
     "ad_select_per_node": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, _VP, _PI64]),
+    "ad_sparsify_binned": (ctypes.c_int, [_VP, _VP, _D, _U64, _VP, _PI64, _PD]),
     "ad_select_whole_graph_noalloc": (ctypes.c_int, [_VP, _I64, _D, ctypes.c_int, _VP, _PI64, _VP]),
     "ad_ml_build": (ctypes.c_int, [_VP, ctypes.POINTER(ad_ml_params), ctypes.POINTER(_VP)]),
     "ad_ml_levels": (ctypes.c_int, [_VP, _PI32]),
@@ -299,6 +300,16 @@ def ad_select_per_node(g, score, e, mode, keep_out):
     nk = ctypes.c_int64()
     _check(load().ad_select_per_node(g, s.ptr, float(e), MODES.get(mode, mode), k.ptr, ctypes.byref(nk)))
     return nk.value
+
+
+def ad_sparsify_binned(g, score, fraction, seed, keep_out):
+    """SparsifyB (Alg. 3) to a target fraction; score None = the handle's distances.
+    Returns (n_kept, e_used)."""
+    s, k = _Arr(score, np.float32), _Arr(keep_out, np.uint8)
+    nk, eu = ctypes.c_int64(), ctypes.c_double()
+    _check(load().ad_sparsify_binned(g, s.ptr, float(fraction), int(seed) & (2**64 - 1), k.ptr, ctypes.byref(nk),
+                                     ctypes.byref(eu)))
+    return nk.value, eu.value
 
 
 def ad_select_whole_graph_noalloc(score, m, fraction, mode, keep_out, stream=None):

@@ -356,6 +356,11 @@ ad_status select_per_node_fit(ad_graph_t g, const float *score_dev, double fract
                               uint8_t *keep_dev, int64_t *n_kept, double *e_used);
 ad_status select_per_node_at(ad_graph_t g, const float *score_dev, double e, ad_mode mode,
                              uint8_t *keep_dev, int64_t *n_kept);
+ad_status select_per_node_fit_ranked(ad_graph_t g, const uint32_t *rank_dev, double fraction, uint8_t *keep_dev,
+                                     int64_t *n_kept, double *e_used);
+
+// SparsifyB order (binned.cu)
+ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev);
 
 ad_status check_scores(ad_graph_t g, const float *score);
 void free_sel_cache(ad_graph_t g);

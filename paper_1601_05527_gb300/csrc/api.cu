@@ -479,6 +479,41 @@ extern "C" ad_status ad_sparsify_scores(ad_graph_t g, const float *score, double
     return st;
 }
 
+extern "C" ad_status ad_sparsify_binned(ad_graph_t g, const float *score, double fraction, uint64_t seed,
+                                        uint8_t *keep_out, int64_t *n_kept, double *e_used) {
+    if (!g) return fail(AD_ERR_INVALID_ARG, "NULL graph");
+    if (!(fraction >= 0.0 && fraction <= 1.0)) return fail(AD_ERR_INVALID_ARG, "fraction must be in [0, 1]");
+    if (!keep_out && g->m > 0) return fail(AD_ERR_INVALID_ARG, "keep_out is NULL");
+    DevBuf tmp_s, tmp_k, ranks;
+    const float *sd = g->rho;
+    if (score) {
+        const void *p = nullptr;
+        AD_TRY(stage_in(g, score, g->m * sizeof(float), tmp_s, &p));
+        sd = static_cast<const float *>(p);
+        AD_TRY(check_scores(g, sd));
+    } else if (!g->have_rho) {
+        return fail(AD_ERR_STATE, "no distances: call ad_algebraic_distance first or pass scores");
+    }
+    const bool dev_out = is_device_ptr(keep_out);
+    uint8_t *kd = keep_out;
+    if (!dev_out) {
+        AD_TRY(ensure(g, tmp_k, g->m + 16));
+        kd = static_cast<uint8_t *>(tmp_k.ptr);
+    }
+    int64_t kept = 0;
+    double e = -1.0;
+    ad_status st = ensure(g, ranks, sizeof(uint32_t) * (g->nnz + 1));
+    if (st == AD_OK) st = binned_ranks(g, sd, seed, static_cast<uint32_t *>(ranks.ptr));
+    if (st == AD_OK) st = select_per_node_fit_ranked(g, static_cast<const uint32_t *>(ranks.ptr), fraction, kd, &kept, &e);
+    if (st == AD_OK && !dev_out) st = copy_out(g, keep_out, kd, g->m);
+    for (DevBuf *b : {&tmp_s, &tmp_k, &ranks})
+        if (b->ptr) dfree(g, b->ptr);
+    if (st != AD_OK) return st;
+    if (n_kept) *n_kept = kept;
+    if (e_used) *e_used = e;
+    return AD_OK;
+}
+
 extern "C" ad_status ad_select_per_node(ad_graph_t g, const float *score, double e, ad_mode mode, uint8_t *keep_out,
                                         int64_t *n_kept) {
     if (!g) return fail(AD_ERR_INVALID_ARG, "NULL graph");

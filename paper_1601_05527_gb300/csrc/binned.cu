@@ -1,0 +1,213 @@
+// binned.cu -- selection order of SparsifyB (Alg. 3) on sm_103a.
+//
+// Per node i of degree d, with the distances rho of its incident edges:
+//   mean and sigma (population) by sequential FP64 sums in CSR order,
+//   bin width h = 3.5 sigma / cbrt(d) (the rule quoted in Sec. 4), bin of an
+//   entry = floor((rho - min) / h), a single bin when sigma = 0;
+//   entries of a bin in order of a Philox word of the edge id, bins in order
+//   of a Philox word of (i, 1 + bin); the selection order is a round robin
+//   over the bins -- round r takes the r-th entry of every bin that has one,
+//   bins in their order -- so every bin contributes before any contributes
+//   twice.  Node i keeps its entries of rank < T(d, e); the union over the two
+//   ends of an edge and the fit of e are those of Alg. 2 (select.cu).
+//
+// Every floating-point step that decides a bin is an explicitly rounded FP64
+// operation (no contraction), in the same order as the plain definition, and
+// cbrt(d) comes from the host's FP64 cbrt, so the bins are exactly those of
+// the definition given the same FP32 distances.
+//
+// Pipeline: per-row statistics (one thread per row, sequential), per-entry
+// bin and Philox word, a stable radix sort by word and then by (row, bin),
+// runs of equal (row, bin) = the non-empty bins, their order inside the row,
+// and per entry the round-robin rank (a pass over the row's bins).
+#include "ad_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace ad {
+
+constexpr uint32_t kBinStream = 0xB1000000u;   // Philox counter word 3 of the binning draws
+constexpr int kBinBits = 24;                   // bins per row < 2^24 (at most ~0.4 d^(5/6) for any data)
+
+__device__ __forceinline__ uint32_t bin_word(uint64_t seed, uint64_t a, uint32_t z) {
+    const uint4 c = make_uint4((uint32_t)a, (uint32_t)(a >> 32), z, kBinStream);
+    return philox4x32_10(c, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32))).x;
+}
+
+// per row: lo = min rho, h = bin width (0: a single bin)
+__global__ void k_bin_stats(const int64_t *rp, const int64_t *eid, const float *score, const int32_t *dc,
+                            const double *cbrt_dc, int64_t n, double *lo_out, double *h_out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p0 = rp[i], d = rp[i + 1] - p0;
+        if (d == 0) continue;
+        double sum = 0.0, lo = (double)score[eid[p0]], hi = lo;
+        for (int64_t t = 0; t < d; ++t) {
+            const double x = (double)score[eid[p0 + t]];
+            sum = __dadd_rn(sum, x);
+            lo = x < lo ? x : lo;
+            hi = x > hi ? x : hi;
+        }
+        const double mean = __ddiv_rn(sum, (double)d);
+        double q = 0.0;
+        for (int64_t t = 0; t < d; ++t) {
+            const double dx = __dsub_rn((double)score[eid[p0 + t]], mean);
+            q = __dadd_rn(q, __dmul_rn(dx, dx));
+        }
+        const double sigma = __dsqrt_rn(__ddiv_rn(q, (double)d));
+        const double h = __ddiv_rn(__dmul_rn(3.5, sigma), cbrt_dc[dc[i]]);
+        lo_out[i] = lo;
+        h_out[i] = (sigma > 0.0 && hi > lo) ? h : 0.0;
+    }
+}
+
+// per entry: its bin and Philox word; keys for the first sort (by word), values = positions
+__global__ void k_bin_entries(const int32_t *erow, const int64_t *eid, const float *score, const double *lo,
+                              const double *h, int64_t nnz, uint64_t seed, uint32_t *bin, uint64_t *keys,
+                              int64_t *vals, unsigned long long *max_bin) {
+    unsigned long long mb = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = erow[p];
+        const double hi_ = h[i];
+        int64_t b = 0;
+        if (hi_ > 0.0) b = (int64_t)floor(__ddiv_rn(__dsub_rn((double)score[eid[p]], lo[i]), hi_));
+        bin[p] = (uint32_t)b;
+        mb = (unsigned long long)b > mb ? (unsigned long long)b : mb;
+        keys[p] = bin_word(seed, (uint64_t)eid[p], 0u);
+        vals[p] = p;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = y > mb ? y : mb;
+    }
+    if ((threadIdx.x & 31) == 0 && mb) atomicMax(max_bin, mb);
+}
+
+// keys of the second sort: (row, bin) of the entry now at each slot
+__global__ void k_bin_rowkeys(const int64_t *vals, const int32_t *erow, const uint32_t *bin, int64_t nnz,
+                              uint64_t *keys) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = vals[s];
+        keys[s] = ((uint64_t)(uint32_t)erow[p] << kBinBits) | bin[p];
+    }
+}
+
+// run starts: slot s begins a non-empty bin when its (row, bin) differs from slot s - 1
+__global__ void k_bin_run_flags(const uint64_t *keys, int64_t nnz, int64_t *flag) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x)
+        flag[s] = (s == 0 || keys[s] != keys[s - 1]) ? 1 : 0;
+}
+
+// the exclusive scan of the run starts counts the starts before a slot; the
+// run of the slot is that count, less one unless the slot starts a run itself
+__global__ void k_bin_inclusive(const int64_t *flag, int64_t nnz, int64_t *run_of) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x)
+        run_of[s] += flag[s] - 1;
+}
+
+// run records: first slot of each run, its bin's Philox word; runs of a row are contiguous
+__global__ void k_bin_runs(const uint64_t *keys, const int64_t *flag, const int64_t *run_of, int64_t nnz, uint64_t seed,
+                           int64_t *run_start, uint32_t *run_word, int64_t *row_runs) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[s]) continue;
+        const int64_t r = run_of[s];
+        const uint64_t k = keys[s];
+        const uint64_t row = k >> kBinBits;
+        const uint32_t b = (uint32_t)(k & ((1u << kBinBits) - 1u));
+        run_start[r] = s;
+        run_word[r] = bin_word(seed, row, 1u + b);
+        if (s == 0 || (keys[s - 1] >> kBinBits) != row) row_runs[row] = r;   // first run of the row
+    }
+}
+
+// per entry: round-robin rank = sum over the row's bins c of min(size_c, r)
+// plus the bins that have an r-th entry and come before the entry's bin,
+// with r the entry's place inside its bin
+__global__ void k_bin_ranks(const uint64_t *keys, const int64_t *vals, const int64_t *run_of, const int64_t *run_start,
+                            const uint32_t *run_word, const int64_t *row_runs, const int64_t *rp, int64_t nnz,
+                            int64_t nruns, uint32_t *rank) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = (int64_t)(keys[s] >> kBinBits);
+        const int64_t r0 = row_runs[row];
+        const int64_t slot_end = rp[row + 1];   // rows keep their CSR ranges in the sorted order
+        const int64_t me = run_of[s];
+        const int64_t r = s - run_start[me];
+        const uint32_t wm = run_word[me];
+        const uint64_t bm = keys[s] & ((1ull << kBinBits) - 1ull);
+        int64_t rk = 0;
+        for (int64_t c = r0; c < nruns && run_start[c] < slot_end; ++c) {
+            const int64_t next = (c + 1 < nruns) ? run_start[c + 1] : nnz;
+            const int64_t size = (next < slot_end ? next : slot_end) - run_start[c];
+            rk += size < r ? size : r;
+            const uint64_t bc = keys[run_start[c]] & ((1ull << kBinBits) - 1ull);
+            const bool before = run_word[c] < wm || (run_word[c] == wm && bc < bm);
+            if (size > r && before) ++rk;
+        }
+        rank[vals[s]] = (uint32_t)rk;
+    }
+}
+
+// Selection rank of every CSR entry under SparsifyB, written to rank_dev[nnz]
+// (device).  score_dev: FP32 distances per edge (device).
+ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev) {
+    const int64_t n = g->n, nnz = g->nnz;
+    if (nnz == 0) return AD_OK;
+    if (n >= ((int64_t)1 << (64 - kBinBits))) return fail(AD_ERR_INVALID_ARG, "graph too large for binned ranks");
+    AD_TRY(ensure_mirror(g));
+    AD_TRY(ensure_degree_classes(g));
+    // cbrt of every distinct degree, from the host's FP64 cbrt
+    std::vector<double> cb(std::max<int32_t>(g->n_deg_classes, 1));
+    for (int32_t q = 0; q < g->n_deg_classes; ++q) cb[q] = std::cbrt((double)g->distinct_degrees[q]);
+    double *cbrt_dc = nullptr, *lo = nullptr, *h = nullptr;
+    uint32_t *bin = nullptr, *run_word = nullptr;
+    uint64_t *keys = nullptr;
+    int64_t *vals = nullptr, *flag = nullptr, *run_of = nullptr, *run_start = nullptr, *row_runs = nullptr;
+    unsigned long long *max_bin = nullptr;
+    AD_TRY(dalloc_t(g, cb.size(), &cbrt_dc));
+    AD_TRY(dalloc_t(g, n + 1, &lo));
+    AD_TRY(dalloc_t(g, n + 1, &h));
+    AD_TRY(dalloc_t(g, nnz, &bin));
+    AD_TRY(dalloc_t(g, nnz, &keys));
+    AD_TRY(dalloc_t(g, nnz, &vals));
+    AD_TRY(dalloc_t(g, 1, &max_bin));
+    AD_TRY(copy_in(g, cbrt_dc, cb.data(), cb.size() * sizeof(double)));
+    AD_CUDA_TRY(cudaMemsetAsync(max_bin, 0, sizeof(unsigned long long), g->stream));
+    const int big = g->num_sms * 16;
+    AD_LAUNCH(k_bin_stats, (int)std::min<int64_t>((n + 127) / 128, big), 128, 0, g->stream, g->rp, g->eid, score_dev,
+              g->deg_class, cbrt_dc, n, lo, h);
+    AD_LAUNCH(k_bin_entries, big, 256, 0, g->stream, g->erow, g->eid, score_dev, lo, h, nnz, seed, bin, keys, vals,
+              max_bin);
+    unsigned long long mb = 0;
+    AD_TRY(copy_out(g, &mb, max_bin, sizeof(mb)));
+    if (mb >= (1ull << kBinBits)) return fail(AD_ERR_INVALID_ARG, "too many bins in one row");
+    AD_TRY(radix_sort_pairs(g, keys, vals, nnz, {0, 8, 16, 24}));            // by Philox word, then position
+    AD_LAUNCH(k_bin_rowkeys, big, 256, 0, g->stream, vals, g->erow, bin, nnz, keys);
+    std::vector<int> shifts;                                                  // bin bits in use, then row bits
+    int bbits = 0;
+    while (bbits < kBinBits && (mb >> bbits) != 0) ++bbits;
+    int rbits = 0;
+    while (rbits < 64 - kBinBits && ((uint64_t)(n - 1) >> rbits) != 0) ++rbits;
+    for (int sh = 0; sh < bbits; sh += 8) shifts.push_back(sh);
+    for (int sh = kBinBits; sh < kBinBits + rbits; sh += 8) shifts.push_back(sh);
+    AD_TRY(radix_sort_pairs(g, keys, vals, nnz, shifts));                     // by (row, bin), stable
+    AD_TRY(dalloc_t(g, nnz, &flag));
+    AD_TRY(dalloc_t(g, nnz, &run_of));
+    AD_LAUNCH(k_bin_run_flags, big, 256, 0, g->stream, keys, nnz, flag);
+    int64_t nruns = 0;
+    AD_TRY(exclusive_scan_i64(g, flag, run_of, nnz, &nruns));
+    AD_TRY(dalloc_t(g, nruns + 1, &run_start));
+    AD_TRY(dalloc_t(g, nruns + 1, &run_word));
+    AD_TRY(dalloc_t(g, n + 1, &row_runs));
+    AD_LAUNCH(k_bin_inclusive, big, 256, 0, g->stream, flag, nnz, run_of);
+    AD_LAUNCH(k_bin_runs, big, 256, 0, g->stream, keys, flag, run_of, nnz, seed, run_start, run_word, row_runs);
+    AD_LAUNCH(k_bin_ranks, big, 256, 0, g->stream, keys, vals, run_of, run_start, run_word, row_runs, g->rp, nnz, nruns,
+              rank_dev);
+    AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    for (void *p : {(void *)cbrt_dc, (void *)lo, (void *)h, (void *)bin, (void *)keys, (void *)vals, (void *)max_bin,
+                    (void *)flag, (void *)run_of, (void *)run_start, (void *)run_word, (void *)row_runs})
+        dfree(g, p);
+    return AD_OK;
+}
+
+}  // namespace ad

@@ -787,7 +787,7 @@ struct ad_graph_s::SelCache {
     int32_t *bseg = nullptr;
     int64_t nb_entries = 0;
     ad::DevBuf info, info_desc, ekey, skey, bvals, T, hist, list_a, list_b, cstar, flag, jsel, kept, st, hist3, ties,
-        tie_off, ddeg, fit, fit_tb, rank2;
+        tie_off, ddeg, fit, fit_tb, rank2, info_other;
     int64_t *epos = nullptr;      // upper CSR entry of every edge
     bool have_ddeg = false;       // ddeg: the distinct degrees on the device
     bool info_valid = false;      // info / info_desc hold the ranks of the handle's own distances
@@ -1124,10 +1124,40 @@ static ad_status select_per_node_fit_host(ad_graph_t g, const int4 *info, double
 
 // The same search with every pass on the device; falls back to host tables
 // when a device T(d, e) is too close to a rounding boundary to be trusted.
+static ad_status fit_search(ad_graph_t g, const int4 *info, double fraction, uint8_t *keep, int64_t *n_kept,
+                            double *e_used);
+
 ad_status select_per_node_fit(ad_graph_t g, const float *score, double fraction, ad_mode mode, uint8_t *keep,
                               int64_t *n_kept, double *e_used) {
     int4 *info = nullptr;
     AD_TRY(per_node_info(g, score, mode, &info));
+    return fit_search(g, info, fraction, keep, n_kept, e_used);
+}
+
+// Per-edge records (rank at each end, degree class of each end) from ranks
+// given per CSR entry in `rank`, then the fit of e and the kept set: Alg. 2's
+// union and search for any per-node selection order (SparsifyB's included).
+ad_status select_per_node_fit_ranked(ad_graph_t g, const uint32_t *rank, double fraction, uint8_t *keep,
+                                     int64_t *n_kept, double *e_used) {
+    AD_TRY(ensure_mirror(g));
+    AD_TRY(ensure_degree_classes(g));
+    ad_graph_s::SelCache *c = nullptr;
+    AD_TRY(sel_cache(g, &c));
+    if (!c->epos) {
+        AD_TRY(dalloc_t(g, g->m + 1, &c->epos));
+        if (g->nnz > 0)
+            AD_LAUNCH(k_edge_pos, g->num_sms * 16, 256, 0, g->stream, g->erow, g->col, g->eid, g->nnz, c->epos);
+    }
+    AD_TRY(ensure(g, c->info_other, 2 * sizeof(int4) * (g->m + 1)));
+    int4 *info = static_cast<int4 *>(c->info_other.ptr);
+    if (g->m > 0)   // the second output (the other order) is not needed: it goes to the spare half
+        AD_LAUNCH(k_info, g->num_sms * 16, 256, 0, g->stream, c->epos, g->mirror, g->erow, g->col, g->deg_class, g->m,
+                  rank, rank, info, info + (g->m + 1));
+    return fit_search(g, info, fraction, keep, n_kept, e_used);
+}
+
+static ad_status fit_search(ad_graph_t g, const int4 *info, double fraction, uint8_t *keep, int64_t *n_kept,
+                            double *e_used) {
     ad_graph_s::SelCache *c = g->sel;
     const int G = g->G;
     const int32_t ndc = std::max<int32_t>(g->n_deg_classes, 1);
