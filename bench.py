@@ -287,6 +287,24 @@ def run_gpu(args):
                             "jaccard_local_30pct_vs_fp32": inter / max(union, 1)}
         del rho32, keep32
 
+    # SparsifyB (Alg. 3) on the same distances, timed on its own (not part of the step)
+    binned = None
+    if args.variants:
+        L.ad_algebraic_distance(h, R, K_SWEEPS, OMEGA, SEED, 0, storage, 0, None)
+        for _ in range(2):
+            L.ad_sparsify_binned(h, None, FRACTION, SEED, keep_d)
+        barrier()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nb = 3
+        b0.record(stream)
+        for _ in range(nb):
+            kb, eb = L.ad_sparsify_binned(h, None, FRACTION, SEED, keep_d)
+        b1.record(stream)
+        barrier()
+        binned = {"ms": b0.elapsed_time(b1) / nb, "kept": kb, "e": eb,
+                  "what": f"SparsifyB to {int(FRACTION * 100)}% per node on the step's distances (bins, round robin, "
+                          "fit of e), timed on its own"}
+
     # phase split and the dominant kernel's launch time (events on the handle's stream)
     L.ad_graph_set_profiling(h, True)
     for ph in ("init", "sweep", "distance", "select"):
@@ -344,6 +362,7 @@ def run_gpu(args):
                              "avg_launch_ms": sweep_ms, "traffic": sweep_traffic(storage)},
                 "gpu_launches": int(launches),
                 "storage_variants": variants or None,
+                "sparsify_binned": binned,
                 "clocks": clk}
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g)

@@ -292,6 +292,18 @@ ad_status ad_sparsify_binned(ad_graph_t g, const float *score, double fraction, 
                              int64_t *n_kept, double *e_used);
 
 /*
+ * Local Degree, the method the paper compares against (Sec. 1.1, Sec. 6;
+ * Lindner et al.): every node takes the edges to its T(d, e) neighbours of
+ * largest degree (ties: smaller neighbour position in the row), an edge is
+ * kept when either end takes it, and e is fitted to reach
+ * K = floor(fraction * m + 1/2) edges as in ad_sparsify's per-node scope.  No
+ * distances are needed.  keep_out[m] uint8, host or device; n_kept, e_used may
+ * be NULL.  Errors: AD_ERR_INVALID_ARG, AD_ERR_OOM, AD_ERR_CUDA.
+ */
+ad_status ad_sparsify_local_degree(ad_graph_t g, double fraction, uint8_t *keep_out, int64_t *n_kept,
+                                   double *e_used);
+
+/*
  * Whole-graph ranking (as ad_sparsify_scores with AD_SCOPE_WHOLE_GRAPH on a
  * single graph whose edge ids are 0..m-1) for callers that cannot let a
  * library allocate device memory -- a process whose device memory is all

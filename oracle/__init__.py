@@ -71,6 +71,8 @@ def _L():
                 "orc_binned_ranks": (ctypes.c_int, [ctypes.c_int64, I64P, I32P, F64P, ctypes.c_uint64, I64P, I64P]),
                 "orc_sparsify_binned": (ctypes.c_int, [ctypes.c_int64, I64P, I32P, F64P, ctypes.c_uint64,
                                                        ctypes.c_double, U8P, I64P, F64P]),
+                "orc_sparsify_local_degree": (ctypes.c_int, [ctypes.c_int64, I64P, I32P, ctypes.c_double, U8P, I64P,
+                                                             F64P]),
                 "orc_create_seeds": (ctypes.c_int, [ctypes.c_int64, I64P, I32P, F64P, ctypes.c_double, U8P]),
                 "orc_aggregate": (ctypes.c_int64, [ctypes.c_int64, I64P, I32P, F64P, U8P, I32P]),
                 "orc_galerkin": (ctypes.c_int64, [ctypes.c_int64, I64P, I32P, F64P, I32P, ctypes.c_int64,
@@ -244,6 +246,20 @@ def sparsify_binned(rp, ci, score, seed, fraction):
                                   fraction, _p(keep, U8P), ctypes.byref(nk), ctypes.byref(eu))
     if st != 0:
         raise RuntimeError(f"oracle binned sparsify failed ({st})")
+    return keep, nk.value, eu.value
+
+
+def sparsify_local_degree(rp, ci, fraction):
+    """Local Degree (the comparison method of Sec. 6): (keep[m] uint8, n_kept, e_used)."""
+    rp, ci, _ = _csr(rp, ci)
+    m = int(_L().orc_count_edges(len(rp) - 1, _p(rp, I64P), _p(ci, I32P)))
+    keep = np.zeros(m, dtype=np.uint8)
+    nk = ctypes.c_int64(0)
+    eu = ctypes.c_double(0)
+    st = _L().orc_sparsify_local_degree(len(rp) - 1, _p(rp, I64P), _p(ci, I32P), fraction, _p(keep, U8P),
+                                        ctypes.byref(nk), ctypes.byref(eu))
+    if st != 0:
+        raise RuntimeError(f"oracle local degree failed ({st})")
     return keep, nk.value, eu.value
 
 

@@ -540,6 +540,55 @@ int orc_sparsify_binned(int64_t n, const int64_t *rp, const int32_t *ci, const d
 }
 
 /* ------------------------------------------------------------------------ */
+/* Local Degree, the comparison method of Sec. 6 (Lindner et al.): node i    */
+/* keeps the edges to its T(d_i, e) neighbours of largest degree (ties: the  */
+/* smaller neighbour id, i.e. CSR position); union and fit of e as Alg. 2.   */
+/* ------------------------------------------------------------------------ */
+typedef struct { int64_t d; int64_t t; int64_t e; } ld_entry;
+
+static int cmp_ld(const void *a, const void *b)
+{
+    const ld_entry *x = (const ld_entry *)a, *y = (const ld_entry *)b;
+    if (x->d != y->d) return x->d > y->d ? -1 : 1;
+    return (x->t < y->t) ? -1 : (x->t > y->t);
+}
+
+int orc_sparsify_local_degree(int64_t n, const int64_t *rp, const int32_t *ci, double fraction, uint8_t *keep,
+                              int64_t *n_kept, double *e_used)
+{
+    if (fraction < 0.0 || fraction > 1.0) return ORC_ERR_ARG;
+    int64_t m = orc_count_edges(n, rp, ci), nnz = rp[n];
+    int64_t K = orc_target_count(m, fraction);
+    int64_t maxd = 0;
+    for (int64_t i = 0; i < n; ++i) if (rp[i + 1] - rp[i] > maxd) maxd = rp[i + 1] - rp[i];
+    int64_t *eid = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t *sorted_e = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    ld_entry *a = (ld_entry *)malloc(sizeof(ld_entry) * (size_t)(maxd > 0 ? maxd : 1));
+    if (!eid || !sorted_e || !a) { free(eid); free(sorted_e); free(a); return ORC_ERR_OOM; }
+    orc_entry_edge_ids(n, rp, ci, eid);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t d = rp[i + 1] - rp[i];
+        for (int64_t t = 0; t < d; ++t) {
+            const int32_t j = ci[rp[i] + t];
+            a[t].d = rp[j + 1] - rp[j];
+            a[t].t = t;
+            a[t].e = eid[rp[i] + t];
+        }
+        qsort(a, (size_t)d, sizeof(ld_entry), cmp_ld);
+        for (int64_t t = 0; t < d; ++t) sorted_e[rp[i] + t] = a[t].e;
+    }
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 40; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (union_of_tops(n, rp, sorted_e, m, mid, keep) >= K) hi = mid; else lo = mid;
+    }
+    *n_kept = union_of_tops(n, rp, sorted_e, m, hi, keep);
+    *e_used = hi;
+    free(eid); free(sorted_e); free(a);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Multilevel framework (Sec. 5, Alg. 6).                                    */
 /* ------------------------------------------------------------------------ */
 

@@ -15,7 +15,7 @@ from ._lib import (  # noqa: F401
     ad_graph_destroy, ad_graph_edge_offsets, ad_graph_export, ad_graph_info, ad_graph_phase_time, ad_graph_set_edge_weights,
     ad_graph_set_profiling, ad_kernel_launch_count, ad_last_error, ad_ml_build, ad_ml_destroy, ad_ml_level_size,
     ad_ml_levels, ad_ml_segment_ratios, ad_ml_sparsify, ad_select_per_node, ad_sparsify, ad_sparsify_binned,
-    ad_sparsify_scores,
+    ad_sparsify_local_degree, ad_sparsify_scores,
     ad_status_string, ad_version, load, use_default_allocator, use_torch_allocator,
 )
 

@@ -72,6 +72,7 @@ _SIGS = {
     "ad_sparsify_scores": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, ctypes.c_int, _VP, _PI64, _PD]),
     "ad_select_per_node": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, _VP, _PI64]),
     "ad_sparsify_binned": (ctypes.c_int, [_VP, _VP, _D, _U64, _VP, _PI64, _PD]),
+    "ad_sparsify_local_degree": (ctypes.c_int, [_VP, _D, _VP, _PI64, _PD]),
     "ad_select_whole_graph_noalloc": (ctypes.c_int, [_VP, _I64, _D, ctypes.c_int, _VP, _PI64, _VP]),
     "ad_ml_build": (ctypes.c_int, [_VP, ctypes.POINTER(ad_ml_params), ctypes.POINTER(_VP)]),
     "ad_ml_levels": (ctypes.c_int, [_VP, _PI32]),
@@ -309,6 +310,14 @@ def ad_sparsify_binned(g, score, fraction, seed, keep_out):
     nk, eu = ctypes.c_int64(), ctypes.c_double()
     _check(load().ad_sparsify_binned(g, s.ptr, float(fraction), int(seed) & (2**64 - 1), k.ptr, ctypes.byref(nk),
                                      ctypes.byref(eu)))
+    return nk.value, eu.value
+
+
+def ad_sparsify_local_degree(g, fraction, keep_out):
+    """Local Degree (the paper's comparison method) to a target fraction: (n_kept, e_used)."""
+    k = _Arr(keep_out, np.uint8)
+    nk, eu = ctypes.c_int64(), ctypes.c_double()
+    _check(load().ad_sparsify_local_degree(g, float(fraction), k.ptr, ctypes.byref(nk), ctypes.byref(eu)))
     return nk.value, eu.value
 
 

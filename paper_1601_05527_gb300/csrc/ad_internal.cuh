@@ -358,6 +358,7 @@ ad_status select_per_node_at(ad_graph_t g, const float *score_dev, double e, ad_
                              uint8_t *keep_dev, int64_t *n_kept);
 ad_status select_per_node_fit_ranked(ad_graph_t g, const uint32_t *rank_dev, double fraction, uint8_t *keep_dev,
                                      int64_t *n_kept, double *e_used);
+ad_status select_local_degree(ad_graph_t g, double fraction, uint8_t *keep_dev, int64_t *n_kept, double *e_used);
 
 // SparsifyB order (binned.cu)
 ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev);

@@ -514,6 +514,29 @@ extern "C" ad_status ad_sparsify_binned(ad_graph_t g, const float *score, double
     return AD_OK;
 }
 
+extern "C" ad_status ad_sparsify_local_degree(ad_graph_t g, double fraction, uint8_t *keep_out, int64_t *n_kept,
+                                              double *e_used) {
+    if (!g) return fail(AD_ERR_INVALID_ARG, "NULL graph");
+    if (!(fraction >= 0.0 && fraction <= 1.0)) return fail(AD_ERR_INVALID_ARG, "fraction must be in [0, 1]");
+    if (!keep_out && g->m > 0) return fail(AD_ERR_INVALID_ARG, "keep_out is NULL");
+    const bool dev_out = is_device_ptr(keep_out);
+    DevBuf tmp;
+    uint8_t *kd = keep_out;
+    if (!dev_out) {
+        AD_TRY(ensure(g, tmp, g->m + 16));
+        kd = static_cast<uint8_t *>(tmp.ptr);
+    }
+    int64_t kept = 0;
+    double e = -1.0;
+    ad_status st = select_local_degree(g, fraction, kd, &kept, &e);
+    if (st == AD_OK && !dev_out) st = copy_out(g, keep_out, kd, g->m);
+    if (tmp.ptr) dfree(g, tmp.ptr);
+    if (st != AD_OK) return st;
+    if (n_kept) *n_kept = kept;
+    if (e_used) *e_used = e;
+    return AD_OK;
+}
+
 extern "C" ad_status ad_select_per_node(ad_graph_t g, const float *score, double e, ad_mode mode, uint8_t *keep_out,
                                         int64_t *n_kept) {
     if (!g) return fail(AD_ERR_INVALID_ARG, "NULL graph");

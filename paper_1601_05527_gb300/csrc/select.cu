@@ -894,34 +894,10 @@ ad_status select_whole_graph(ad_graph_t g, const float *score, double fraction, 
     return AD_OK;
 }
 
-// Ranks of every CSR entry in both orders, gathered per edge: the info of
-// Alg. 2.  For the handle's own distances the result is kept until they change.
-static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, int4 **info_out) {
-    AD_TRY(ensure_mirror(g));
-    AD_TRY(ensure_degree_classes(g));
-    ad_graph_s::SelCache *c = nullptr;
-    AD_TRY(sel_cache(g, &c));
-    AD_TRY(rank_lists(g, c));
-    const int64_t nnz = g->nnz;
-    AD_TRY(ensure(g, c->info, sizeof(int4) * (g->m + 1)));
-    AD_TRY(ensure(g, c->info_desc, sizeof(int4) * (g->m + 1)));
-    int4 *info_asc = static_cast<int4 *>(c->info.ptr), *info_desc = static_cast<int4 *>(c->info_desc.ptr);
-    *info_out = mode == AD_MODE_GLOBAL ? info_desc : info_asc;
-    const bool own = score == g->rho && g->have_rho;
-    if (own && c->info_valid && c->info_version == g->rho_version) return AD_OK;
-    c->info_valid = false;
-    if (!c->epos) {
-        AD_TRY(dalloc_t(g, g->m + 1, &c->epos));
-        if (nnz > 0)
-            AD_LAUNCH(k_edge_pos, g->num_sms * 16, 256, 0, g->stream, g->erow, g->col, g->eid, nnz, c->epos);
-    }
-    AD_TRY(ensure(g, c->rank2, 2 * sizeof(uint32_t) * (nnz + 1)));
-    RankOut out;
-    out.asc = static_cast<uint32_t *>(c->rank2.ptr);
-    out.desc = out.asc + (nnz + 1);
-    AD_TRY(ensure(g, c->ekey, sizeof(uint32_t) * (nnz + 1)));
-    uint32_t *ekey = static_cast<uint32_t *>(c->ekey.ptr);
-    if (nnz > 0) AD_LAUNCH(k_entry_keys, g->num_sms * 16, 256, 0, g->stream, g->eid, nnz, score, 0, ekey);
+// Ranks of every CSR entry inside its row by (ekey, position), ascending, in
+// both orders (RankOut), by degree class: register counting, warp and CTA
+// bitonic sorts, and the radix sort for rows above the CTA sort's capacity.
+static ad_status entry_ranks(ad_graph_t g, ad_graph_s::SelCache *c, const uint32_t *ekey, RankOut out) {
     auto wblocks = [&](int64_t rows_, int per_warp) {
         return (int)std::max<int64_t>(1, std::min<int64_t>((rows_ + 8 * per_warp - 1) / (8 * per_warp),
                                                            (int64_t)g->num_sms * 32));
@@ -961,6 +937,38 @@ static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, i
         AD_TRY(radix_sort_pairs(g, keys, vals, nb, shifts));
         AD_LAUNCH(k_big_ranks, blocks, 256, 0, g->stream, keys, vals, nb, c->bstart, out);
     }
+    return AD_OK;
+}
+
+// Ranks of every CSR entry in both orders, gathered per edge: the info of
+// Alg. 2.  For the handle's own distances the result is kept until they change.
+static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, int4 **info_out) {
+    AD_TRY(ensure_mirror(g));
+    AD_TRY(ensure_degree_classes(g));
+    ad_graph_s::SelCache *c = nullptr;
+    AD_TRY(sel_cache(g, &c));
+    AD_TRY(rank_lists(g, c));
+    const int64_t nnz = g->nnz;
+    AD_TRY(ensure(g, c->info, sizeof(int4) * (g->m + 1)));
+    AD_TRY(ensure(g, c->info_desc, sizeof(int4) * (g->m + 1)));
+    int4 *info_asc = static_cast<int4 *>(c->info.ptr), *info_desc = static_cast<int4 *>(c->info_desc.ptr);
+    *info_out = mode == AD_MODE_GLOBAL ? info_desc : info_asc;
+    const bool own = score == g->rho && g->have_rho;
+    if (own && c->info_valid && c->info_version == g->rho_version) return AD_OK;
+    c->info_valid = false;
+    if (!c->epos) {
+        AD_TRY(dalloc_t(g, g->m + 1, &c->epos));
+        if (nnz > 0)
+            AD_LAUNCH(k_edge_pos, g->num_sms * 16, 256, 0, g->stream, g->erow, g->col, g->eid, nnz, c->epos);
+    }
+    AD_TRY(ensure(g, c->rank2, 2 * sizeof(uint32_t) * (nnz + 1)));
+    RankOut out;
+    out.asc = static_cast<uint32_t *>(c->rank2.ptr);
+    out.desc = out.asc + (nnz + 1);
+    AD_TRY(ensure(g, c->ekey, sizeof(uint32_t) * (nnz + 1)));
+    uint32_t *ekey = static_cast<uint32_t *>(c->ekey.ptr);
+    if (nnz > 0) AD_LAUNCH(k_entry_keys, g->num_sms * 16, 256, 0, g->stream, g->eid, nnz, score, 0, ekey);
+    AD_TRY(entry_ranks(g, c, ekey, out));
     if (g->m > 0)
         AD_LAUNCH(k_info, g->num_sms * 16, 256, 0, g->stream, c->epos, g->mirror, g->erow, g->col, g->deg_class, g->m,
                   out.asc, out.desc, info_asc, info_desc);
@@ -1154,6 +1162,35 @@ ad_status select_per_node_fit_ranked(ad_graph_t g, const uint32_t *rank, double 
         AD_LAUNCH(k_info, g->num_sms * 16, 256, 0, g->stream, c->epos, g->mirror, g->erow, g->col, g->deg_class, g->m,
                   rank, rank, info, info + (g->m + 1));
     return fit_search(g, info, fraction, keep, n_kept, e_used);
+}
+
+// key of entry (i, j) for Local Degree: larger degree of j first
+__global__ void k_ld_keys(const int64_t *rp, const int32_t *col, int64_t nnz, uint32_t *ekey) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = col[p];
+        ekey[p] = ~(uint32_t)(rp[j + 1] - rp[j]);
+    }
+}
+
+// Local Degree (the comparison method of Sec. 1.1 and Sec. 6): node i takes the
+// edges to its T(d_i, e) neighbours of largest degree (ties: smaller CSR
+// position); union and fit of e as Alg. 2.
+ad_status select_local_degree(ad_graph_t g, double fraction, uint8_t *keep, int64_t *n_kept, double *e_used) {
+    AD_TRY(ensure_mirror(g));
+    AD_TRY(ensure_degree_classes(g));
+    ad_graph_s::SelCache *c = nullptr;
+    AD_TRY(sel_cache(g, &c));
+    AD_TRY(rank_lists(g, c));
+    const int64_t nnz = g->nnz;
+    AD_TRY(ensure(g, c->ekey, sizeof(uint32_t) * (nnz + 1)));
+    AD_TRY(ensure(g, c->rank2, 2 * sizeof(uint32_t) * (nnz + 1)));
+    uint32_t *ekey = static_cast<uint32_t *>(c->ekey.ptr);
+    RankOut out;
+    out.asc = static_cast<uint32_t *>(c->rank2.ptr);
+    out.desc = out.asc + (nnz + 1);
+    if (nnz > 0) AD_LAUNCH(k_ld_keys, g->num_sms * 16, 256, 0, g->stream, g->rp, g->col, nnz, ekey);
+    AD_TRY(entry_ranks(g, c, ekey, out));
+    return select_per_node_fit_ranked(g, out.asc, fraction, keep, n_kept, e_used);
 }
 
 static ad_status fit_search(ad_graph_t g, const int4 *info, double fraction, uint8_t *keep, int64_t *n_kept,
