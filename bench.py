@@ -296,10 +296,12 @@ def run_gpu(args):
         barrier()
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         nb = 3
+        torch.cuda.nvtx.range_push("binned")
         b0.record(stream)
         for _ in range(nb):
             kb, eb = L.ad_sparsify_binned(h, None, FRACTION, SEED, keep_d)
         b1.record(stream)
+        torch.cuda.nvtx.range_pop()
         barrier()
         binned = {"ms": b0.elapsed_time(b1) / nb, "kept": kb, "e": eb,
                   "what": f"SparsifyB to {int(FRACTION * 100)}% per node on the step's distances (bins, round robin, "

@@ -67,9 +67,10 @@
  *       contributes before any contributes twice.  Random order = ascending
  *       word 0 of Philox4x32-10 with key = the selection seed and counter
  *       (edge id lo, hi, 0, 0xB1000000) for an entry, (vertex lo, hi, 1 + bin,
- *       0xB1000000) for a bin; ties by position / bin index.  Sums for mean
- *       and sigma run sequentially in CSR order.  Union over the two ends of
- *       an edge and the fit of e are those of Alg. 2 (R8).
+ *       0xB1000000) for a bin; ties by position / bin index.  The statistics
+ *       and bins are computed in FP32 (distances are FP32 values), sums
+ *       sequentially in CSR order, cbrt(d) as FP64 cbrt rounded to FP32.  Union
+ *       over the two ends of an edge and the fit of e are those of Alg. 2 (R8).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -430,8 +431,10 @@ static int cmp_bin_key(const void *a, const void *b)
 /*
  * Selection rank of every CSR entry under SparsifyB; node i keeps its entries
  * of rank < T(d_i, e).  For row i with distances rho_1..rho_d (CSR order):
- *   mean and sigma (population) by sequential FP64 sums in CSR order;
- *   sigma == 0: one bin; else h = 3.5 sigma / cbrt(d), bin = floor((rho - min) / h);
+ *   mean and sigma (population) by sequential FP32 sums in CSR order;
+ *   sigma == 0: one bin; else h = 3.5 sigma / cbrt(d), bin = floor((rho - min) / h),
+ *   all in FP32 with each operation rounded on its own (cbrt(d): FP64 cbrt
+ *   rounded to FP32);
  *   entries of a bin in order of (Philox word of the edge id, position);
  *   bins in order of (Philox word of (i, 1 + bin), bin);
  *   selection order = round robin over the bins: round r takes the r-th entry
@@ -459,25 +462,27 @@ int orc_binned_ranks(int64_t n, const int64_t *rp, const int32_t *ci, const doub
     for (int64_t i = 0; i < n; ++i) {
         const int64_t p0 = rp[i], d = rp[i + 1] - p0;
         if (d == 0) continue;
-        double sum = 0.0, lo = score[eid[p0]], hi = lo;
+        /* FP32 throughout, each operation rounded on its own (reading R13) */
+        float sum = 0.0f, lo = (float)score[eid[p0]], hi = lo;
         for (int64_t t = 0; t < d; ++t) {
-            const double x = score[eid[p0 + t]];
-            sum += x;
+            const float x = (float)score[eid[p0 + t]];
+            sum = sum + x;
             if (x < lo) lo = x;
             if (x > hi) hi = x;
         }
-        const double mean = sum / (double)d;
-        double q = 0.0;
+        const float mean = sum / (float)d;
+        float q = 0.0f;
         for (int64_t t = 0; t < d; ++t) {
-            const double dx = score[eid[p0 + t]] - mean;
-            q += dx * dx;
+            const float dx = (float)score[eid[p0 + t]] - mean;
+            const float sq = dx * dx;
+            q = q + sq;
         }
-        const double sigma = sqrt(q / (double)d);
-        const double h = 3.5 * sigma / cbrt((double)d);
+        const float sigma = sqrtf(q / (float)d);
+        const float h = 3.5f * sigma / (float)cbrt((double)d);
         int64_t nbins = 1;
         for (int64_t t = 0; t < d; ++t) {
             int64_t b = 0;
-            if (sigma > 0.0 && hi > lo) b = (int64_t)floor((score[eid[p0 + t]] - lo) / h);
+            if (sigma > 0.0f && hi > lo) b = (int64_t)floorf(((float)score[eid[p0 + t]] - lo) / h);
             a[t].bin = b;
             a[t].u = bin_word(seed, (uint64_t)eid[p0 + t], 0u);
             a[t].t = t;

@@ -1,7 +1,7 @@
 // binned.cu -- selection order of SparsifyB (Alg. 3) on sm_103a.
 //
 // Per node i of degree d, with the distances rho of its incident edges:
-//   mean and sigma (population) by sequential FP64 sums in CSR order,
+//   mean and sigma (population) by sequential FP32 sums in CSR order,
 //   bin width h = 3.5 sigma / cbrt(d) (the rule quoted in Sec. 4), bin of an
 //   entry = floor((rho - min) / h), a single bin when sigma = 0;
 //   entries of a bin in order of a Philox word of the edge id, bins in order
@@ -11,10 +11,12 @@
 //   twice.  Node i keeps its entries of rank < T(d, e); the union over the two
 //   ends of an edge and the fit of e are those of Alg. 2 (select.cu).
 //
-// Every floating-point step that decides a bin is an explicitly rounded FP64
+// Every floating-point step that decides a bin is an explicitly rounded FP32
 // operation (no contraction), in the same order as the plain definition, and
-// cbrt(d) comes from the host's FP64 cbrt, so the bins are exactly those of
-// the definition given the same FP32 distances.
+// cbrt(d) comes from the host's FP64 cbrt rounded to FP32, so the bins are
+// exactly those of the definition given the same FP32 distances.  (FP32, not
+// FP64: the per-row sums are long dependent chains, and FP64 runs on a narrow
+// pipe on this part.)
 //
 // Pipeline: per-row statistics (one thread per row, sequential), per-entry
 // bin and Philox word, a stable radix sort by word and then by (row, bin),
@@ -36,42 +38,54 @@ __device__ __forceinline__ uint32_t bin_word(uint64_t seed, uint64_t a, uint32_t
     return philox4x32_10(c, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32))).x;
 }
 
-// per row: lo = min rho, h = bin width (0: a single bin)
-__global__ void k_bin_stats(const int64_t *rp, const int64_t *eid, const float *score, const int32_t *dc,
-                            const double *cbrt_dc, int64_t n, double *lo_out, double *h_out) {
+// the distance of every CSR entry, in CSR order, so that the per-row sums
+// below read one contiguous run instead of chasing edge ids
+__global__ void k_bin_gather(const int64_t *eid, const float *score, int64_t nnz, float *xs) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        xs[p] = score[eid[p]];
+}
+
+// per row: lo = min rho, h = bin width (0: a single bin); FP32 with every
+// operation rounded on its own, sums sequential in CSR order, as the
+// definition states them
+__global__ void k_bin_stats(const int64_t *rp, const float *xs, const int32_t *dc, const float *cbrt_dc, int64_t n,
+                            float *lo_out, float *h_out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p0 = rp[i], d = rp[i + 1] - p0;
         if (d == 0) continue;
-        double sum = 0.0, lo = (double)score[eid[p0]], hi = lo;
+        const float *x = xs + p0;
+        float sum = 0.f, lo = x[0], hi = lo;
+#pragma unroll 8
         for (int64_t t = 0; t < d; ++t) {
-            const double x = (double)score[eid[p0 + t]];
-            sum = __dadd_rn(sum, x);
-            lo = x < lo ? x : lo;
-            hi = x > hi ? x : hi;
+            const float v = x[t];
+            sum = __fadd_rn(sum, v);
+            lo = v < lo ? v : lo;
+            hi = v > hi ? v : hi;
         }
-        const double mean = __ddiv_rn(sum, (double)d);
-        double q = 0.0;
+        const float mean = __fdiv_rn(sum, (float)d);
+        float q = 0.f;
+#pragma unroll 8
         for (int64_t t = 0; t < d; ++t) {
-            const double dx = __dsub_rn((double)score[eid[p0 + t]], mean);
-            q = __dadd_rn(q, __dmul_rn(dx, dx));
+            const float dx = __fsub_rn(x[t], mean);
+            q = __fadd_rn(q, __fmul_rn(dx, dx));
         }
-        const double sigma = __dsqrt_rn(__ddiv_rn(q, (double)d));
-        const double h = __ddiv_rn(__dmul_rn(3.5, sigma), cbrt_dc[dc[i]]);
+        const float sigma = __fsqrt_rn(__fdiv_rn(q, (float)d));
+        const float h = __fdiv_rn(__fmul_rn(3.5f, sigma), cbrt_dc[dc[i]]);
         lo_out[i] = lo;
-        h_out[i] = (sigma > 0.0 && hi > lo) ? h : 0.0;
+        h_out[i] = (sigma > 0.f && hi > lo) ? h : 0.f;
     }
 }
 
 // per entry: its bin and Philox word; keys for the first sort (by word), values = positions
-__global__ void k_bin_entries(const int32_t *erow, const int64_t *eid, const float *score, const double *lo,
-                              const double *h, int64_t nnz, uint64_t seed, uint32_t *bin, uint64_t *keys,
+__global__ void k_bin_entries(const int32_t *erow, const int64_t *eid, const float *xs, const float *lo,
+                              const float *h, int64_t nnz, uint64_t seed, uint32_t *bin, uint64_t *keys,
                               int64_t *vals, unsigned long long *max_bin) {
     unsigned long long mb = 0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = erow[p];
-        const double hi_ = h[i];
+        const float hi_ = h[i];
         int64_t b = 0;
-        if (hi_ > 0.0) b = (int64_t)floor(__ddiv_rn(__dsub_rn((double)score[eid[p]], lo[i]), hi_));
+        if (hi_ > 0.f) b = (int64_t)floorf(__fdiv_rn(__fsub_rn(xs[p], lo[i]), hi_));
         bin[p] = (uint32_t)b;
         mb = (unsigned long long)b > mb ? (unsigned long long)b : mb;
         keys[p] = bin_word(seed, (uint64_t)eid[p], 0u);
@@ -157,9 +171,9 @@ ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint
     AD_TRY(ensure_mirror(g));
     AD_TRY(ensure_degree_classes(g));
     // cbrt of every distinct degree, from the host's FP64 cbrt
-    std::vector<double> cb(std::max<int32_t>(g->n_deg_classes, 1));
-    for (int32_t q = 0; q < g->n_deg_classes; ++q) cb[q] = std::cbrt((double)g->distinct_degrees[q]);
-    double *cbrt_dc = nullptr, *lo = nullptr, *h = nullptr;
+    std::vector<float> cb(std::max<int32_t>(g->n_deg_classes, 1));
+    for (int32_t q = 0; q < g->n_deg_classes; ++q) cb[q] = (float)std::cbrt((double)g->distinct_degrees[q]);
+    float *cbrt_dc = nullptr, *lo = nullptr, *h = nullptr, *xs = nullptr;
     uint32_t *bin = nullptr, *run_word = nullptr;
     uint64_t *keys = nullptr;
     int64_t *vals = nullptr, *flag = nullptr, *run_of = nullptr, *run_start = nullptr, *row_runs = nullptr;
@@ -167,17 +181,18 @@ ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint
     AD_TRY(dalloc_t(g, cb.size(), &cbrt_dc));
     AD_TRY(dalloc_t(g, n + 1, &lo));
     AD_TRY(dalloc_t(g, n + 1, &h));
+    AD_TRY(dalloc_t(g, nnz, &xs));
     AD_TRY(dalloc_t(g, nnz, &bin));
     AD_TRY(dalloc_t(g, nnz, &keys));
     AD_TRY(dalloc_t(g, nnz, &vals));
     AD_TRY(dalloc_t(g, 1, &max_bin));
-    AD_TRY(copy_in(g, cbrt_dc, cb.data(), cb.size() * sizeof(double)));
+    AD_TRY(copy_in(g, cbrt_dc, cb.data(), cb.size() * sizeof(float)));
     AD_CUDA_TRY(cudaMemsetAsync(max_bin, 0, sizeof(unsigned long long), g->stream));
     const int big = g->num_sms * 16;
-    AD_LAUNCH(k_bin_stats, (int)std::min<int64_t>((n + 127) / 128, big), 128, 0, g->stream, g->rp, g->eid, score_dev,
-              g->deg_class, cbrt_dc, n, lo, h);
-    AD_LAUNCH(k_bin_entries, big, 256, 0, g->stream, g->erow, g->eid, score_dev, lo, h, nnz, seed, bin, keys, vals,
-              max_bin);
+    AD_LAUNCH(k_bin_gather, big, 256, 0, g->stream, g->eid, score_dev, nnz, xs);
+    AD_LAUNCH(k_bin_stats, (int)std::min<int64_t>((n + 127) / 128, big), 128, 0, g->stream, g->rp, xs, g->deg_class,
+              cbrt_dc, n, lo, h);
+    AD_LAUNCH(k_bin_entries, big, 256, 0, g->stream, g->erow, g->eid, xs, lo, h, nnz, seed, bin, keys, vals, max_bin);
     unsigned long long mb = 0;
     AD_TRY(copy_out(g, &mb, max_bin, sizeof(mb)));
     if (mb >= (1ull << kBinBits)) return fail(AD_ERR_INVALID_ARG, "too many bins in one row");
@@ -204,7 +219,7 @@ ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint
     AD_LAUNCH(k_bin_ranks, big, 256, 0, g->stream, keys, vals, run_of, run_start, run_word, row_runs, g->rp, nnz, nruns,
               rank_dev);
     AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    for (void *p : {(void *)cbrt_dc, (void *)lo, (void *)h, (void *)bin, (void *)keys, (void *)vals, (void *)max_bin,
+    for (void *p : {(void *)cbrt_dc, (void *)lo, (void *)h, (void *)xs, (void *)bin, (void *)keys, (void *)vals, (void *)max_bin,
                     (void *)flag, (void *)run_of, (void *)run_start, (void *)run_word, (void *)row_runs})
         dfree(g, p);
     return AD_OK;
