@@ -30,7 +30,13 @@
 #define AD_SWEEP_UB 4          // independent row loads in flight per lane
 #endif
 #ifndef AD_SWEEP_MINB
-#define AD_SWEEP_MINB 4        // minimum resident CTAs per SM requested from ptxas
+#define AD_SWEEP_MINB 6        // resident CTAs per SM requested from ptxas for the FP32 sweep
+#endif
+#ifndef AD_SWEEP_MINB16
+#define AD_SWEEP_MINB16 5      // ... for the 16-bit storage formats
+#endif
+#ifndef AD_DIST_MINB
+#define AD_DIST_MINB 4         // ... for the distance pass
 #endif
 #ifndef AD_MAX_LPR
 #define AD_MAX_LPR 32          // most lanes that share one row (more chunks go to each lane beyond it)
@@ -386,8 +392,13 @@ struct LaneStats {
 // ----------------------------------------------------------------------------
 // One JOR sweep (Alg. 1 inner loop) over all rows of degree > 0.
 // ----------------------------------------------------------------------------
+// More warps per SM hide more of the gather latency even at the cost of a few
+// spilled registers: measured best at 6 CTAs (FP32) and 5 (16-bit) per SM.
+template <typename T>
+constexpr int sweep_minb() { return sizeof(T) == 4 ? AD_SWEEP_MINB : AD_SWEEP_MINB16; }
+
 template <typename T, int LPR, int CPL>
-__global__ void __launch_bounds__(256, AD_SWEEP_MINB) k_sweep(SweepArgs a) {
+__global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
     using L = Lane<T, LPR, CPL>;
     constexpr int V = L::V, E = L::E, G = L::G;
     extern __shared__ float sm[];   // [2][warps][stride]
@@ -643,7 +654,7 @@ __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64
 }
 
 template <typename T, int LPR, int CPL>
-__global__ void __launch_bounds__(256, AD_SWEEP_MINB) k_distance(SweepArgs a) {
+__global__ void __launch_bounds__(256, AD_DIST_MINB) k_distance(SweepArgs a) {
     using L = Lane<T, LPR, CPL>;
     constexpr int V = L::V, E = L::E, G = L::G;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
