@@ -162,9 +162,11 @@ struct Lane {
 // a time, coalesced, and broadcast with shuffles; each lane then issues up to
 // UB independent 16-byte row loads before it consumes any of them, so that
 // enough requests are in flight to cover the L2 latency.
-template <typename T, int LPR, int CPL>
-__device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int64_t p1, int lane, int grp,
-                                            int gl, float (&acc)[CPL * Store<T>::V]) {
+// W: edge weights present; without them no weight is read or broadcast and
+// the rows are plainly added (the same sums as fmaf with weight 1).
+template <typename T, int LPR, int CPL, bool W>
+__device__ __forceinline__ void warp_gather_w(const SweepArgs &a, int64_t p0, int64_t p1, int lane, int grp,
+                                              int gl, float (&acc)[CPL * Store<T>::V]) {
     using L = Lane<T, LPR, CPL>;
     constexpr int V = L::V, G = L::G;
     constexpr int U = 32 / G;                       // neighbours per group per batch of 32
@@ -178,7 +180,7 @@ __device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int6
         float wj = 0.f;
         if (p < p1) {
             cj = ld_stream(a.col + p);
-            wj = a.w ? ld_stream(a.w + p) : 1.f;
+            if (W) wj = ld_stream(a.w + p);
         }
         const int cnt = (int)(p1 - base < 32 ? p1 - base : 32);
 #pragma unroll
@@ -190,7 +192,7 @@ __device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int6
             for (int u = 0; u < UB; ++u) {
                 const int src = (u0 + u) * G + grp;
                 const int32_t nb = __shfl_sync(0xffffffffu, cj, src);
-                wt[u] = __shfl_sync(0xffffffffu, wj, src);
+                if (W) wt[u] = __shfl_sync(0xffffffffu, wj, src);
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
                     const int q = gl + c * LPR;
@@ -204,18 +206,29 @@ __device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int6
                     float f[V];
                     Store<T>::unpack(v[u][c], f);
 #pragma unroll
-                    for (int e = 0; e < V; ++e) acc[c * V + e] = fmaf(wt[u], f[e], acc[c * V + e]);
+                    for (int e = 0; e < V; ++e)
+                        acc[c * V + e] = W ? fmaf(wt[u], f[e], acc[c * V + e]) : acc[c * V + e] + f[e];
                 }
         }
     }
 }
 
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int64_t p1, int lane, int grp,
+                                            int gl, float (&acc)[CPL * Store<T>::V]) {
+    if (!a.w) {   // the weighted loop reads a.w: it is reached only with weights present
+        warp_gather_w<T, LPR, CPL, false>(a, p0, p1, lane, grp, gl, acc);
+        return;
+    }
+    warp_gather_w<T, LPR, CPL, true>(a, p0, p1, lane, grp, gl, acc);
+}
+
 // Gather-accumulate a short row (<= kSmallUnroll entries per round) with one
 // lane group: all of its column indices, then all row loads, then the sums.
 constexpr int kSmallUnroll = AD_SWEEP_UB;
-template <typename T, int LPR, int CPL>
-__device__ __forceinline__ void group_gather(const SweepArgs &a, int64_t p0, int64_t p1, int gl,
-                                             float (&acc)[CPL * Store<T>::V]) {
+template <typename T, int LPR, int CPL, bool W>
+__device__ __forceinline__ void group_gather_w(const SweepArgs &a, int64_t p0, int64_t p1, int gl,
+                                               float (&acc)[CPL * Store<T>::V]) {
     constexpr int V = Store<T>::V;
     constexpr int UB = (kSmallUnroll / CPL) > 0 ? (kSmallUnroll / CPL) : 1;
     const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
@@ -227,7 +240,7 @@ __device__ __forceinline__ void group_gather(const SweepArgs &a, int64_t p0, int
         for (int u = 0; u < UB; ++u) {
             const bool ok = base + u < p1;
             nb[u] = ok ? ld_stream(a.col + base + u) : 0;
-            wt[u] = ok ? (a.w ? ld_stream(a.w + base + u) : 1.f) : 0.f;
+            if (W) wt[u] = ok ? ld_stream(a.w + base + u) : 0.f;
         }
         uint4 v[UB][CPL];
 #pragma unroll
@@ -244,9 +257,20 @@ __device__ __forceinline__ void group_gather(const SweepArgs &a, int64_t p0, int
                 float f[V];
                 Store<T>::unpack(v[u][c], f);
 #pragma unroll
-                for (int e = 0; e < V; ++e) acc[c * V + e] = fmaf(wt[u], f[e], acc[c * V + e]);
+                for (int e = 0; e < V; ++e)
+                    acc[c * V + e] = W ? fmaf(wt[u], f[e], acc[c * V + e]) : acc[c * V + e] + f[e];
             }
     }
+}
+
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void group_gather(const SweepArgs &a, int64_t p0, int64_t p1, int gl,
+                                             float (&acc)[CPL * Store<T>::V]) {
+    if (!a.w) {   // the weighted loop reads a.w: it is reached only with weights present
+        group_gather_w<T, LPR, CPL, false>(a, p0, p1, gl, acc);
+        return;
+    }
+    group_gather_w<T, LPR, CPL, true>(a, p0, p1, gl, acc);
 }
 
 // Sum over the G groups of a warp (butterfly: every group ends with the total).
