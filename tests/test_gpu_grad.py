@@ -11,7 +11,7 @@ from gpu_util import lib
 
 pytestmark = pytest.mark.gpu
 
-GRAD_TOL = 1e-3     # spec bound: relative error against the FP64 reverse mode
+GRAD_TOL = 1e-3     # relative error bound against the FP64 reverse mode (normwise max)
 
 
 def weighted(g, seed):
