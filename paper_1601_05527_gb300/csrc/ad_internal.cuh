@@ -332,6 +332,8 @@ ad_status graph_setup(ad_graph_t g, int32_t flags);
 ad_status build_row_plan(ad_graph_t g, int groups, int small_max, bool upper_only, RowPlan &plan);
 ad_status ensure_mirror(ad_graph_t g);   // also builds erow and eid
 ad_status ensure_degree_classes(ad_graph_t g);
+ad_status partition_by_class(ad_graph_t g, const int8_t *cls, int64_t n, int nclasses, int32_t *order,
+                             std::vector<int64_t> &start);
 ad_status recompute_degrees(ad_graph_t g);
 
 // algebraic distance (sweep.cu).  With keep: the stored vectors after sweep

@@ -47,7 +47,14 @@ __global__ void k_bin_gather(const int64_t *eid, const float *score, int64_t nnz
 
 // per row: lo = min rho, h = bin width (0: a single bin); FP32 with every
 // operation rounded on its own, sums sequential in CSR order, as the
-// definition states them
+// definition states them.  The sums are one dependent chain per row, so the
+// loads run a block of 32 ahead of it (kept in registers).
+constexpr int kStatBlock = 32;
+__device__ __forceinline__ void stat_load(const float *x, int64_t base, int64_t d, float (&buf)[kStatBlock]) {
+#pragma unroll
+    for (int u = 0; u < kStatBlock; ++u) buf[u] = base + u < d ? x[base + u] : 0.f;
+}
+
 __global__ void k_bin_stats(const int64_t *rp, const float *xs, const int32_t *dc, const float *cbrt_dc, int64_t n,
                             float *lo_out, float *h_out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -55,19 +62,36 @@ __global__ void k_bin_stats(const int64_t *rp, const float *xs, const int32_t *d
         if (d == 0) continue;
         const float *x = xs + p0;
         float sum = 0.f, lo = x[0], hi = lo;
-#pragma unroll 8
-        for (int64_t t = 0; t < d; ++t) {
-            const float v = x[t];
-            sum = __fadd_rn(sum, v);
-            lo = v < lo ? v : lo;
-            hi = v > hi ? v : hi;
+        float cur[kStatBlock], nxt[kStatBlock];
+        stat_load(x, 0, d, cur);
+        for (int64_t t0 = 0; t0 < d; t0 += kStatBlock) {
+            if (t0 + kStatBlock < d) stat_load(x, t0 + kStatBlock, d, nxt);
+#pragma unroll
+            for (int u = 0; u < kStatBlock; ++u) {
+                if (t0 + u < d) {
+                    const float v = cur[u];
+                    sum = __fadd_rn(sum, v);
+                    lo = v < lo ? v : lo;
+                    hi = v > hi ? v : hi;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kStatBlock; ++u) cur[u] = nxt[u];
         }
         const float mean = __fdiv_rn(sum, (float)d);
         float q = 0.f;
-#pragma unroll 8
-        for (int64_t t = 0; t < d; ++t) {
-            const float dx = __fsub_rn(x[t], mean);
-            q = __fadd_rn(q, __fmul_rn(dx, dx));
+        stat_load(x, 0, d, cur);
+        for (int64_t t0 = 0; t0 < d; t0 += kStatBlock) {
+            if (t0 + kStatBlock < d) stat_load(x, t0 + kStatBlock, d, nxt);
+#pragma unroll
+            for (int u = 0; u < kStatBlock; ++u) {
+                if (t0 + u < d) {
+                    const float dx = __fsub_rn(cur[u], mean);
+                    q = __fadd_rn(q, __fmul_rn(dx, dx));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kStatBlock; ++u) cur[u] = nxt[u];
         }
         const float sigma = __fsqrt_rn(__fdiv_rn(q, (float)d));
         const float h = __fdiv_rn(__fmul_rn(3.5f, sigma), cbrt_dc[dc[i]]);

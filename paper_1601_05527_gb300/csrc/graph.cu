@@ -407,6 +407,35 @@ __global__ void k_class_scatter(const int8_t *cls, int64_t n, const int64_t *off
     }
 }
 
+// Stable partition of rows 0..n-1 by cls[i] in [0, nclasses) (negative: left
+// out): order lists the rows class by class, by increasing id inside a class;
+// start[c] is the first slot of class c, start[nclasses] the number of rows kept.
+ad_status partition_by_class(ad_graph_t g, const int8_t *cls, int64_t n, int nclasses, int32_t *order,
+                             std::vector<int64_t> &start) {
+    start.assign(nclasses + 1, 0);
+    if (n == 0) return AD_OK;
+    if (nclasses > kClasses) return fail(AD_ERR_INVALID_ARG, "too many classes");
+    const int64_t tiles = (n + kPartThreads - 1) / kPartThreads;
+    int64_t *counts = nullptr, *offs = nullptr, *at_d = nullptr, *picked = nullptr;
+    AD_TRY(dalloc_t(g, (size_t)kClasses * tiles, &counts));
+    AD_TRY(dalloc_t(g, (size_t)kClasses * tiles, &offs));
+    AD_LAUNCH(k_class_counts, (int)tiles, kPartThreads, 0, g->stream, cls, n, counts, tiles);
+    int64_t total = 0;
+    AD_TRY(exclusive_scan_i64(g, counts, offs, (int64_t)kClasses * tiles, &total));
+    AD_LAUNCH(k_class_scatter, (int)tiles, kPartThreads, 0, g->stream, cls, n, offs, tiles, order);
+    std::vector<int64_t> at(nclasses);
+    for (int c = 0; c < nclasses; ++c) at[c] = (int64_t)c * tiles;
+    AD_TRY(dalloc_t(g, nclasses, &at_d));
+    AD_TRY(dalloc_t(g, nclasses, &picked));
+    AD_TRY(copy_in(g, at_d, at.data(), nclasses * sizeof(int64_t)));
+    AD_LAUNCH(k_pick_i64, 1, kClasses, 0, g->stream, offs, at_d, (int64_t)nclasses, (int64_t)kClasses * tiles, total,
+              picked);
+    AD_TRY(copy_out(g, start.data(), picked, nclasses * sizeof(int64_t)));
+    start[nclasses] = total;
+    for (void *p : {(void *)counts, (void *)offs, (void *)at_d, (void *)picked}) dfree(g, p);
+    return AD_OK;
+}
+
 // Class of a row for a plan: -1 inactive, 0 big, 1..10 medium by decreasing
 // log2 degree, 11 small.
 __global__ void k_row_class(const int64_t *rp, const int64_t *upos, int64_t n, int small_max, int upper,

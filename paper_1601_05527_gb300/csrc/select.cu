@@ -499,13 +499,18 @@ __global__ void k_info(const int64_t *epos, const int64_t *mirror, const int32_t
 // rank class of every row: 0 none, 1 d <= 8, 2 d <= 32, 3 d <= 64, 4 d <= 128, 5 d <= 256, 6 d <= 512,
 // 7 d <= kSortCap, 8 larger
 constexpr int kRankClasses = 9;
-__global__ void k_rank_classes(const int64_t *rp, int64_t n, uint8_t *flags /* [kRankClasses - 1][n] */) {
+__global__ void k_rank_classes(const int64_t *rp, int64_t n, int8_t *cls /* class - 1; -1 for degree 0 */) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = rp[i + 1] - rp[i];
         const int c = d == 0 ? 0 : d <= 8 ? 1 : d <= 32 ? 2 : d <= 64 ? 3 : d <= 128 ? 4 : d <= 256 ? 5 : d <= 512 ? 6
                     : d <= kSortCap ? 7 : 8;
-        for (int k = 1; k < kRankClasses; ++k) flags[(int64_t)(k - 1) * n + i] = c == k ? 1 : 0;
+        cls[i] = (int8_t)(c - 1);
     }
+}
+
+__global__ void k_widen_rows(const int32_t *order, int64_t n, int64_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = order[i];
 }
 
 // First candidate (1..nc) at which the edge is kept, nc + 1 when it is not kept
@@ -817,11 +822,25 @@ static ad_status rank_lists(ad_graph_t g, ad_graph_s::SelCache *c) {
     if (c->have_lists) return AD_OK;
     const int64_t n = g->n;
     constexpr int NC = kRankClasses - 1;
-    uint8_t *flags = nullptr;
-    AD_TRY(dalloc_t(g, NC * (n + 1), &flags));
-    if (n > 0) AD_LAUNCH(k_rank_classes, g->num_sms * 8, 256, 0, g->stream, g->rp, n, flags);
-    for (int k = 0; k < NC; ++k) AD_TRY(compact_flags(g, flags + (int64_t)k * n, n, &c->rows[k], &c->nrows[k]));
-    dfree(g, flags);
+    // one stable partition of the rows by class (rows of class k, by increasing id, at start[k])
+    int8_t *cls = nullptr;
+    int32_t *order = nullptr;
+    int64_t *rows_all = nullptr;
+    AD_TRY(dalloc_t(g, n + 1, &cls));
+    AD_TRY(dalloc_t(g, n + 1, &order));
+    AD_TRY(dalloc_t(g, n + 1, &rows_all));
+    if (n > 0) AD_LAUNCH(k_rank_classes, g->num_sms * 8, 256, 0, g->stream, g->rp, n, cls);
+    std::vector<int64_t> start;
+    AD_TRY(partition_by_class(g, cls, n, NC, order, start));
+    if (start[NC] > 0)
+        AD_LAUNCH(k_widen_rows, (int)std::min<int64_t>((start[NC] + 255) / 256, (int64_t)g->num_sms * 16), 256, 0,
+                  g->stream, order, start[NC], rows_all);
+    for (int k = 0; k < NC; ++k) {
+        c->rows[k] = rows_all + start[k];
+        c->nrows[k] = start[k + 1] - start[k];
+    }
+    dfree(g, cls);
+    dfree(g, order);
     const int64_t nbig = c->nrows[NC - 1];
     if (nbig > 0) {
         int64_t *deg = nullptr;
