@@ -208,6 +208,9 @@ def run_gpu(args):
     h = L.ad_graph_create(g.n, rp_d, col_d, None, 0, stream)
     keep_d = torch.empty(g.m, dtype=torch.uint8, device=dev)
     storage = args.storage
+    # launch shape of the sweep chosen by the library's autotuner (setup, not timed)
+    lpr, cpl, per_sm = L.ad_graph_autotune(h, R, storage)
+    shape = {"lanes_per_row": lpr, "chunks_per_lane": cpl, "ctas_per_sm": per_sm or "max", "chosen_by": "ad_graph_autotune"}
 
     def step(handle, keep):
         L.ad_algebraic_distance(handle, R, K_SWEEPS, OMEGA, SEED, 0, storage, 0, None)
@@ -349,7 +352,7 @@ def run_gpu(args):
                 "data": "synthetic",
                 "config": {"workload": workload(), "n": g.n, "n_active": n_active, "m": g.m, "nnz": g.nnz,
                            "R": R, "k": K_SWEEPS, "storage": storage, "graph_digest": g.digest(),
-                           "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "parallelism": "replicas" if ws > 1 else "single GPU", "sweep_shape": shape,
                            "l2": "no flush: per-sweep traffic (column indices 126 MB + vector block) exceeds the 129 MB L2"},
                 "phases_ms_per_step": {"init": phase["init"][0] / prof_steps, "sweeps": phase["sweep"][0] / prof_steps,
                                        "distance": phase["distance"][0] / prof_steps,

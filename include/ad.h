@@ -270,6 +270,21 @@ ad_status ad_select_per_node(ad_graph_t g, const float *score, double e, ad_mode
                              int64_t *n_kept);
 
 /*
+ * Picks the launch shape of the JOR sweep (Alg. 1) for this graph, R and
+ * storage by timing the candidates on the handle: lanes per row (the natural
+ * 16-byte-chunk layout, and half as many lanes with two chunks each) x
+ * resident CTAs per SM (as many as fit, 5, 4).  Each candidate runs a short
+ * distance computation (k = 4) three times; the fastest shape is kept on the
+ * handle and used by every later call with this R and storage.  The result
+ * depends only on the shape through the order of FP32 additions.
+ *   lanes_per_row, chunks_per_lane, ctas_per_sm (0 = as many as fit): the
+ *   chosen shape; each may be NULL.
+ * Errors: AD_ERR_INVALID_ARG, AD_ERR_OOM, AD_ERR_CUDA.
+ */
+ad_status ad_graph_autotune(ad_graph_t g, int32_t R, ad_storage storage, int32_t *lanes_per_row,
+                            int32_t *chunks_per_lane, int32_t *ctas_per_sm);
+
+/*
  * SparsifyB, the binned ("mixture") single-level sparsification of Alg. 3
  * (Sec. 4): for every node, the distances of its incident edges are put into
  * bins of width h = 3.5 sigma / d^(1/3) (sigma: their population standard

@@ -12,7 +12,7 @@ from . import graphgen  # noqa: F401
 from ._lib import (  # noqa: F401
     ADError, AD_DIST_KEEP_STATE, AD_DIST_NORMALIZE, AD_CREATE_SKIP_VALIDATION, MODES, SCOPES, STORAGES,
     ad_algebraic_distance, ad_algebraic_distance_backward, ad_coarsen, ad_graph_create, ad_graph_create_batched,
-    ad_graph_destroy, ad_graph_edge_offsets, ad_graph_export, ad_graph_info, ad_graph_phase_time, ad_graph_set_edge_weights,
+    ad_graph_autotune, ad_graph_destroy, ad_graph_edge_offsets, ad_graph_export, ad_graph_info, ad_graph_phase_time, ad_graph_set_edge_weights,
     ad_graph_set_profiling, ad_kernel_launch_count, ad_last_error, ad_ml_build, ad_ml_destroy, ad_ml_level_size,
     ad_ml_levels, ad_ml_segment_ratios, ad_ml_sparsify, ad_select_per_node, ad_sparsify, ad_sparsify_binned,
     ad_sparsify_local_degree, ad_sparsify_scores,

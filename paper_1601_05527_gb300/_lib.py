@@ -72,6 +72,7 @@ _SIGS = {
     "ad_sparsify_scores": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, ctypes.c_int, _VP, _PI64, _PD]),
     "ad_select_per_node": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, _VP, _PI64]),
     "ad_sparsify_binned": (ctypes.c_int, [_VP, _VP, _D, _U64, _VP, _PI64, _PD]),
+    "ad_graph_autotune": (ctypes.c_int, [_VP, _I32, ctypes.c_int, _PI32, _PI32, _PI32]),
     "ad_sparsify_local_degree": (ctypes.c_int, [_VP, _D, _VP, _PI64, _PD]),
     "ad_select_whole_graph_noalloc": (ctypes.c_int, [_VP, _I64, _D, ctypes.c_int, _VP, _PI64, _VP]),
     "ad_ml_build": (ctypes.c_int, [_VP, ctypes.POINTER(ad_ml_params), ctypes.POINTER(_VP)]),
@@ -301,6 +302,15 @@ def ad_select_per_node(g, score, e, mode, keep_out):
     nk = ctypes.c_int64()
     _check(load().ad_select_per_node(g, s.ptr, float(e), MODES.get(mode, mode), k.ptr, ctypes.byref(nk)))
     return nk.value
+
+
+def ad_graph_autotune(g, R, storage="fp32"):
+    """Choose the sweep's launch shape for (R, storage) by timing; returns
+    (lanes_per_row, chunks_per_lane, ctas_per_sm) (0: as many as fit)."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ad_graph_autotune(g, int(R), STORAGES.get(storage, storage), ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def ad_sparsify_binned(g, score, fraction, seed, keep_out):

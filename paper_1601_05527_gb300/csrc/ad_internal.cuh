@@ -290,6 +290,12 @@ struct ad_graph_s {
     SelCache *sel = nullptr;
     ad::DevBuf scan_ws;
 
+    // sweep shapes chosen by ad_graph_autotune, per (R, storage)
+    struct Tuned {
+        int32_t R, storage, lpr, cpl, per_sm;
+    };
+    std::vector<Tuned> tuned;
+
     // CUDA graph of the launch sequence of a repeated ad_algebraic_distance call
     struct Replay {
         bool have_key = false;      // key / ptrs describe the last call
@@ -350,6 +356,7 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
 ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, const void *x_in, void *x_out,
                      const uint32_t *pmin, const uint32_t *pmax, uint32_t *mn, uint32_t *mx);
 ad_status get_row_plan(ad_graph_t g, int groups, bool upper, RowPlan **out);
+void natural_shape(int R, ad_storage storage, int *lanes_per_row, int *chunks_per_lane);   // sweep.cu
 
 // selection (select.cu)
 ad_status select_whole_graph(ad_graph_t g, const float *score_dev, double fraction, ad_mode mode,

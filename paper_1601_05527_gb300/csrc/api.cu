@@ -3,6 +3,7 @@
 // select.cu, multilevel.cu and grad.cu.
 #include "ad_internal.cuh"
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -418,6 +419,69 @@ extern "C" ad_status ad_algebraic_distance(ad_graph_t g, int32_t R, int32_t k, d
     g->have_rho = true;
     g->rho_version++;
     if (rho_out) AD_TRY(copy_out(g, rho_out, g->rho, g->m * sizeof(float)));
+    return AD_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Autotuning of the sweep shape
+// ----------------------------------------------------------------------------
+extern "C" ad_status ad_graph_autotune(ad_graph_t g, int32_t R, ad_storage storage, int32_t *lanes_per_row,
+                                       int32_t *chunks_per_lane, int32_t *ctas_per_sm) {
+    if (!g) return fail(AD_ERR_INVALID_ARG, "NULL graph");
+    if (R < 1 || R > 256) return fail(AD_ERR_INVALID_ARG, "R must be in [1, 256]");
+    if (storage < AD_STORAGE_FP32 || storage > AD_STORAGE_Q16) return fail(AD_ERR_INVALID_ARG, "bad storage");
+    drop_replay(g);   // a recorded launch sequence holds the old shape
+    auto &tv = g->tuned;
+    tv.erase(std::remove_if(tv.begin(), tv.end(),
+                            [&](const ad_graph_s::Tuned &t) { return t.R == R && t.storage == (int32_t)storage; }),
+             tv.end());
+    int nat_lpr = 1, nat_cpl = 1;
+    natural_shape(R, storage, &nat_lpr, &nat_cpl);
+    struct Cand { int lpr, cpl, per_sm; };
+    std::vector<Cand> cands;
+    std::vector<std::pair<int, int>> shapes = {{nat_lpr, nat_cpl}};
+    if (nat_lpr >= 2 && nat_cpl == 1) shapes.push_back({nat_lpr / 2, 2});
+    for (const auto &sh : shapes)
+        for (int per_sm : {0, 5, 4}) cands.push_back({sh.first, sh.second, per_sm});
+    int best = 0;
+    float best_ms = 0.f;
+    if (g->m > 0) {
+        float *rho = nullptr;
+        AD_TRY(dalloc_t(g, g->m + 1, &rho));
+        cudaEvent_t e0, e1;
+        AD_CUDA_TRY(cudaEventCreate(&e0));
+        AD_CUDA_TRY(cudaEventCreate(&e1));
+        const bool prof = g->profiling;
+        g->profiling = false;
+        ad_status st = AD_OK;
+        for (size_t c = 0; c < cands.size() && st == AD_OK; ++c) {
+            tv.push_back({R, (int32_t)storage, cands[c].lpr, cands[c].cpl, cands[c].per_sm});
+            float t_best = 0.f;
+            for (int rep = 0; rep < 3 && st == AD_OK; ++rep) {   // the first run builds the row plans
+                cudaEventRecord(e0, g->stream);
+                st = algebraic_distance(g, R, 4, 0.5, 1, 0, storage, 0, rho);
+                cudaEventRecord(e1, g->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(AD_ERR_CUDA, "autotune timing");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && (rep == 1 || ms < t_best)) t_best = ms;
+            }
+            tv.pop_back();
+            if (st == AD_OK && (c == 0 || t_best < best_ms)) {
+                best = (int)c;
+                best_ms = t_best;
+            }
+        }
+        g->profiling = prof;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        dfree(g, rho);
+        AD_TRY(st);
+    }
+    tv.push_back({R, (int32_t)storage, cands[best].lpr, cands[best].cpl, cands[best].per_sm});
+    if (lanes_per_row) *lanes_per_row = cands[best].lpr;
+    if (chunks_per_lane) *chunks_per_lane = cands[best].cpl;
+    if (ctas_per_sm) *ctas_per_sm = cands[best].per_sm;
     return AD_OK;
 }
 

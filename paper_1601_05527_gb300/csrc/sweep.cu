@@ -19,7 +19,10 @@ ad_status launch_init(ad_graph_t g, ad_storage storage, int blocks, int32_t stri
     }
 }
 
-static Config pick_config(int R, ad_storage storage) {
+// Natural shape: the row's 16-byte chunks, rounded up to a power of two, over
+// as many lanes as possible (at most AD_MAX_LPR); a shape chosen by
+// ad_graph_autotune for this (R, storage) replaces it.
+Config natural_config(int R, ad_storage storage) {
     Config c;
     c.V = storage == AD_STORAGE_FP32 ? 4 : 8;
     c.nchunks = (R + c.V - 1) / c.V;
@@ -28,6 +31,23 @@ static Config pick_config(int R, ad_storage storage) {
     c.lpr = p2 < AD_MAX_LPR ? p2 : AD_MAX_LPR;
     c.cpl = p2 / c.lpr;
     c.stride = p2 * c.V;
+    return c;
+}
+
+void natural_shape(int R, ad_storage storage, int *lpr, int *cpl) {
+    const Config c = natural_config(R, storage);
+    *lpr = c.lpr;
+    *cpl = c.cpl;
+}
+
+static Config pick_config(ad_graph_t g, int R, ad_storage storage) {
+    Config c = natural_config(R, storage);
+    for (const auto &t : g->tuned)
+        if (t.R == R && t.storage == (int32_t)storage) {
+            c.lpr = t.lpr;
+            c.cpl = t.cpl;
+            c.per_sm = t.per_sm;
+        }
     return c;
 }
 
@@ -82,7 +102,7 @@ static void ev_end(ad_graph_t g, double &acc, int64_t &cnt) {
 // nullptr = none) reducing min/max into mn/mx; used to recompute iterates.
 ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, const void *x_in, void *x_out,
                      const uint32_t *pmin, const uint32_t *pmax, uint32_t *mn, uint32_t *mx) {
-    const Config cf = pick_config(R, storage);
+    const Config cf = pick_config(g, R, storage);
     RowPlan *sp = nullptr;
     AD_TRY(get_plan(g, 32 / cf.lpr, false, &sp));
     AD_TRY(ensure(g, g->part, (size_t)(sp->n_big > 0 ? sp->n_big : 1) * cf.stride * sizeof(float)));
@@ -107,7 +127,7 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
                              uint32_t stream_id, ad_storage storage, int32_t flags, float *rho_dev,
                              const KeepSpec *keep) {
     if (g->m == 0) return AD_OK;   // no edges: nothing to relax and no distance to write
-    const Config cf = pick_config(R, storage);
+    const Config cf = pick_config(g, R, storage);
     const int groups = 32 / cf.lpr;
     const size_t esz = storage == AD_STORAGE_FP32 ? 4 : 2;
     const size_t xbytes = ((size_t)g->n + 1) * cf.stride * esz;

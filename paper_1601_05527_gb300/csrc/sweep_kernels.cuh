@@ -416,6 +416,34 @@ struct LaneStats {
 // ----------------------------------------------------------------------------
 // One JOR sweep (Alg. 1 inner loop) over all rows of degree > 0.
 // ----------------------------------------------------------------------------
+// Sum of the partial rows of one high-degree row (its chunks t0 .. t0 +
+// nchunk - 1): group g adds partials g, g + G, ... in order, then the groups'
+// sums are added (once per high-degree row).
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void sum_partials(const SweepArgs &a, int64_t t0, int32_t nchunk, int grp, int gl, float (&S)[CPL * Store<T>::V]) {
+    constexpr int V = Store<T>::V, E = CPL * V, G = 32 / LPR;
+#pragma unroll
+    for (int e = 0; e < E; ++e) S[e] = 0.f;
+    for (int32_t cc2 = grp; cc2 < nchunk; cc2 += G) {
+        const float4 *pp = reinterpret_cast<const float4 *>(a.part + (t0 + cc2) * (int64_t)a.stride);
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+            const int q = gl + cc * LPR;
+            if (q < a.nchunks) {
+#pragma unroll
+                for (int e4 = 0; e4 < V / 4; ++e4) {
+                    const float4 f = __ldcg(pp + (q * V) / 4 + e4);
+                    S[cc * V + 4 * e4 + 0] += f.x;
+                    S[cc * V + 4 * e4 + 1] += f.y;
+                    S[cc * V + 4 * e4 + 2] += f.z;
+                    S[cc * V + 4 * e4 + 3] += f.w;
+                }
+            }
+        }
+    }
+    reduce_groups<LPR, E>(S);
+}
+
 // More warps per SM hide more of the gather latency even at the cost of a few
 // spilled registers: measured best at 6 CTAs (FP32) and 5 (16-bit) per SM.
 template <typename T>
@@ -471,26 +499,7 @@ __global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
                 uint4 own[CPL];
                 load_own<T, LPR, CPL>(a, row, gl, own);
                 float S[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) S[e] = 0.f;
-                for (int32_t cc2 = grp; cc2 < nchunk; cc2 += G) {
-                    const float4 *pp = reinterpret_cast<const float4 *>(a.part + (t0 + cc2) * (int64_t)a.stride);
-#pragma unroll
-                    for (int cc = 0; cc < CPL; ++cc) {
-                        const int q = gl + cc * LPR;
-                        if (q < a.nchunks) {
-#pragma unroll
-                            for (int e4 = 0; e4 < V / 4; ++e4) {
-                                const float4 f = __ldcg(pp + (q * V) / 4 + e4);
-                                S[cc * V + 4 * e4 + 0] += f.x;
-                                S[cc * V + 4 * e4 + 1] += f.y;
-                                S[cc * V + 4 * e4 + 2] += f.z;
-                                S[cc * V + 4 * e4 + 3] += f.w;
-                            }
-                        }
-                    }
-                }
-                reduce_groups<LPR, E>(S);
+                sum_partials<T, LPR, CPL>(a, t0, nchunk, grp, gl, S);
                 if (grp == 0) {
                     ls.enter(a, gl, row_graph(row), true);
                     row_epilogue<T, LPR, CPL>(a, row, gl, own, S, ls.acg, ls.mn, ls.mx);
@@ -728,6 +737,7 @@ __global__ void __launch_bounds__(256, AD_DIST_MINB) k_distance(SweepArgs a) {
 
 struct Config {
     int lpr, cpl, V, stride, nchunks;
+    int per_sm = 0;   // sweep CTAs per SM (0: as many as fit)
 };
 
 
@@ -760,6 +770,7 @@ ad_status dispatch(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &
     auto run = [&](auto lpr_c, auto cpl_c) -> ad_status {
         constexpr int LPR = decltype(lpr_c)::value, CPL = decltype(cpl_c)::value;
         int per_sm = blocks_for<T, LPR, CPL>(sweep, smem);
+        if (sweep && cf.per_sm > 0 && cf.per_sm < per_sm) per_sm = cf.per_sm;
         int64_t blocks = (int64_t)per_sm * g->num_sms;
         const int64_t need = (n_tasks + 7) / 8;
         if (blocks > need) blocks = need > 0 ? need : 1;
@@ -775,13 +786,12 @@ ad_status dispatch(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &
         case 1601: return run(integral_constant<int, 16>{}, integral_constant<int, 1>{});
         case 3201: return run(integral_constant<int, 32>{}, integral_constant<int, 1>{});
         case 3202: return run(integral_constant<int, 32>{}, integral_constant<int, 2>{});
-#if AD_MAX_LPR < 32
+        // fewer lanes per row, more chunks per lane: the alternative shapes the autotuner tries
+        case 102: return run(integral_constant<int, 1>{}, integral_constant<int, 2>{});
         case 202: return run(integral_constant<int, 2>{}, integral_constant<int, 2>{});
-        case 204: return run(integral_constant<int, 2>{}, integral_constant<int, 4>{});
         case 402: return run(integral_constant<int, 4>{}, integral_constant<int, 2>{});
-        case 404: return run(integral_constant<int, 4>{}, integral_constant<int, 4>{});
         case 802: return run(integral_constant<int, 8>{}, integral_constant<int, 2>{});
-#endif
+        case 1602: return run(integral_constant<int, 16>{}, integral_constant<int, 2>{});
         default: return fail(AD_ERR_INVALID_ARG, "unsupported R / storage combination");
     }
 }

@@ -221,3 +221,24 @@ def test_repeated_calls_replay_the_same_results():
     assert_rho_close(rho, oracle.algebraic_distance(g2.row_ptr, g2.col, g2.weight.astype(np.float64), R=16, k=12,
                                                     omega=0.5, seed=4))
     L.ad_graph_destroy(h)
+
+
+@pytest.mark.parametrize("storage,R", [("fp32", 32), ("fp16", 32), ("bf16", 16), ("fp32", 8)])
+def test_autotuned_shape_keeps_the_distances(storage, R):
+    """After ad_graph_autotune the handle uses the chosen sweep shape; the
+    distances stay within tolerance of the oracle (FP32) or equal to the
+    untuned run up to FP32 summation order (16-bit storage)."""
+    L = lib()
+    g = graphgen.rmat(13, 16, seed=4)
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
+    before = np.zeros(g.m, np.float32)
+    L.ad_algebraic_distance(h, R, 12, 0.5, 3, 0, storage, 0, before)
+    lpr, cpl, per_sm = L.ad_graph_autotune(h, R, storage)
+    assert lpr >= 1 and cpl in (1, 2) and per_sm in (0, 4, 5)
+    after = np.zeros(g.m, np.float32)
+    L.ad_algebraic_distance(h, R, 12, 0.5, 3, 0, storage, 0, after)
+    L.ad_graph_destroy(h)
+    if storage == "fp32":
+        assert_rho_close(after, ref_rho(g, R, 12, 0.5, seed=3))
+    else:
+        assert rho_error(after, before.astype(np.float64)) < 0.05
