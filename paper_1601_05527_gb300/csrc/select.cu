@@ -245,7 +245,7 @@ __device__ __forceinline__ void put_ranks(const RankOut &o, int64_t p, int d, ui
     o.desc[p] = (uint32_t)d - leq + (r_asc - lt);
 }
 
-constexpr int kSortCap = 4096;      // rows up to this degree are sorted by one CTA (32 KB of shared memory)
+constexpr int kSortCap = 4096;      // rows up to this degree are sorted by one CTA in shared memory
 
 // rows of degree <= GS (8 or 32): a group of GS lanes per row, one entry per
 // lane, rank = number of smaller (key, position) pairs in the row
@@ -371,23 +371,7 @@ __global__ void __launch_bounds__(256) k_rank_wsort(const int64_t *rp, const int
     }
 }
 
-// Bitonic sort of up to kSortCap 64-bit keys (key << 32 | position) in smem.
-__device__ void block_bitonic(unsigned long long *a, int len_pow2) {
-    for (int size = 2; size <= len_pow2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < len_pow2 / 2; t += blockDim.x) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = ((lo & size) == 0);
-                const unsigned long long x = a[lo], y = a[hi];
-                if ((x > y) == up) { a[lo] = y; a[hi] = x; }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// rows of degree in (512, kSortCap]: a CTA per row, bitonic sort of (key, position)
+// first index of a sorted shared-memory array holding a value >= v
 __device__ __forceinline__ int lower_bound_smem(const unsigned long long *a, int n, unsigned long long v) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -397,18 +381,80 @@ __device__ __forceinline__ int lower_bound_smem(const unsigned long long *a, int
     return lo;
 }
 
-__global__ void k_rank_mid(const int64_t *rp, const int64_t *rows, const uint32_t *ekey, RankOut out) {
-    __shared__ unsigned long long a[kSortCap];
+// Rows of degree in (512, kSortCap]: one CTA per row sorts (key << 32 |
+// position) with a stable LSD radix sort in shared memory (8-bit digits; a
+// digit pass whose keys all share one digit is skipped).  Each warp owns a
+// contiguous segment; inside a 32-entry chunk, entries with equal digits are
+// ordered by lane (__match_any_sync), warps in segment order: stable.
+constexpr int kMidThreads = 256, kMidWarps = kMidThreads / 32;
+static_assert(kMidThreads == 256, "one thread per 8-bit digit");
+constexpr size_t kMidSmem = 2 * kSortCap * sizeof(unsigned long long) + kMidWarps * 256 * sizeof(uint32_t);
+
+__global__ void __launch_bounds__(kMidThreads) k_rank_mid(const int64_t *rp, const int64_t *rows, const uint32_t *ekey,
+                                                          RankOut out) {
+    extern __shared__ unsigned long long mid_sm[];
+    unsigned long long *a = mid_sm, *b = mid_sm + kSortCap;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(mid_sm + 2 * kSortCap);   // [warp][256] counts, then offsets
+    __shared__ uint32_t base[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t row = rows[blockIdx.x];
     const int64_t p0 = rp[row];
     const int d = (int)(rp[row + 1] - p0);
-    int len2 = 1;
-    while (len2 < d) len2 <<= 1;
-    for (int t = threadIdx.x; t < len2; t += blockDim.x)
-        a[t] = t < d ? (((unsigned long long)ekey[p0 + t] << 32) | (unsigned)t) : ~0ull;
+    for (int t = threadIdx.x; t < d; t += kMidThreads) a[t] = ((unsigned long long)ekey[p0 + t] << 32) | (unsigned)t;
+    const int seg = (((d + kMidWarps - 1) / kMidWarps) + 31) & ~31;           // entries per warp, whole chunks
+    const int s0 = warp * seg, s1 = min(d, s0 + seg);
+    const unsigned lt_mask = (1u << lane) - 1u;
     __syncthreads();
-    block_bitonic(a, len2);
-    for (int t = threadIdx.x; t < d; t += blockDim.x) {
+    for (int shift = 32; shift < 64; shift += 8) {
+        for (int q = lane; q < 256; q += 32) cnt[warp * 256 + q] = 0;
+        __syncwarp();
+        for (int c = s0; c < s1; c += 32) {                                       // per-warp digit counts
+            const int t = c + lane;
+            const int dg = t < s1 ? (int)((a[t] >> shift) & 0xff) : 256;
+            const unsigned peers = __match_any_sync(0xffffffffu, dg);
+            if (dg < 256 && (peers & lt_mask) == 0) cnt[warp * 256 + dg] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        int skip;
+        {   // thread q: digit q's total over warps, then offsets digit-major, warp-minor
+            const int q = threadIdx.x;
+            uint32_t tot = 0;
+            for (int w = 0; w < kMidWarps; ++w) tot += cnt[w * 256 + q];
+            base[q] = tot;
+            skip = __syncthreads_or(tot == (uint32_t)d);                          // one digit holds all
+            for (int o = 1; o < 256; o <<= 1) {                                  // inclusive scan of base
+                const uint32_t y = q >= o ? base[q - o] : 0u;
+                __syncthreads();
+                base[q] += y;
+                __syncthreads();
+            }
+            uint32_t run = base[q] - tot;                                         // exclusive
+            for (int w = 0; w < kMidWarps; ++w) {
+                const uint32_t c2 = cnt[w * 256 + q];
+                cnt[w * 256 + q] = run;
+                run += c2;
+            }
+        }
+        __syncthreads();
+        if (skip) continue;                                                       // the order is unchanged
+        for (int c = s0; c < s1; c += 32) {                                       // stable scatter
+            const int t = c + lane;
+            const bool live = t < s1;
+            const unsigned long long v = live ? a[t] : 0ull;
+            const int dg = live ? (int)((v >> shift) & 0xff) : 256;
+            const unsigned peers = __match_any_sync(0xffffffffu, dg);
+            if (live) b[cnt[warp * 256 + dg] + __popc(peers & lt_mask)] = v;
+            __syncwarp();
+            if (live && (peers & lt_mask) == 0) cnt[warp * 256 + dg] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        unsigned long long *tmp = a;
+        a = b;
+        b = tmp;
+    }
+    for (int t = threadIdx.x; t < d; t += kMidThreads) {
         const unsigned long long k32 = a[t] & 0xffffffff00000000ull;
         // tie runs need a search; a key unlike both neighbours is its own run
         const int lt = (t > 0 && (a[t - 1] & 0xffffffff00000000ull) == k32) ? lower_bound_smem(a, d, k32) : t;
@@ -417,6 +463,22 @@ __global__ void k_rank_mid(const int64_t *rp, const int64_t *rows, const uint32_
                             : t + 1;
         put_ranks(out, p0 + (int64_t)(a[t] & 0xffffffffull), d, (uint32_t)t, (uint32_t)lt, (uint32_t)leq);
     }
+}
+
+// k_rank_mid needs more than the default 48 KB of dynamic shared memory: opt in
+// once per device (the attribute belongs to the current device's context)
+static ad_status set_mid_smem() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    AD_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return fail(AD_ERR_CUDA, "device index out of range");
+    if (!done[dev]) {
+        AD_CUDA_TRY(cudaFuncSetAttribute(k_rank_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmem));
+        done[dev] = true;
+    }
+    return AD_OK;
 }
 
 // Rows of degree > kSortCap.  Their entries are listed once per handle
@@ -941,8 +1003,10 @@ static ad_status entry_ranks(ad_graph_t g, ad_graph_s::SelCache *c, const uint32
     if (nr[5] > 0)
         AD_LAUNCH(k_rank_wsort<16>, wblocks(nr[5], 1), 256, 0, g->stream, g->rp, rows[5],
                   nr[5], ekey, out);
-    if (nr[6] > 0)
-        AD_LAUNCH(k_rank_mid, (int)nr[6], 256, 0, g->stream, g->rp, rows[6], ekey, out);
+    if (nr[6] > 0) {
+        AD_TRY(set_mid_smem());
+        AD_LAUNCH(k_rank_mid, (int)nr[6], kMidThreads, kMidSmem, g->stream, g->rp, rows[6], ekey, out);
+    }
     if (c->nb_entries > 0) {
         const int64_t nb = c->nb_entries, nbig = nr[7];
         AD_TRY(ensure(g, c->skey, sizeof(uint64_t) * nb));
