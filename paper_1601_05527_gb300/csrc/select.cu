@@ -384,8 +384,10 @@ __device__ __forceinline__ int lower_bound_smem(const unsigned long long *a, int
 // Rows of degree in (512, kSortCap]: one CTA per row sorts (key << 32 |
 // position) with a stable LSD radix sort in shared memory (8-bit digits; a
 // digit pass whose keys all share one digit is skipped).  Each warp owns a
-// contiguous segment; inside a 32-entry chunk, entries with equal digits are
-// ordered by lane (__match_any_sync), warps in segment order: stable.
+// contiguous segment of whole 32-entry chunks.  Digit counts are shared-memory
+// atomics per warp; the offsets run digit-major, warp-minor; inside a chunk,
+// entries with equal digits keep lane order (their peer mask comes from one
+// ballot per digit bit), so every pass is stable.  Four barriers per pass.
 constexpr int kMidThreads = 256, kMidWarps = kMidThreads / 32;
 static_assert(kMidThreads == 256, "one thread per 8-bit digit");
 constexpr size_t kMidSmem = 2 * kSortCap * sizeof(unsigned long long) + kMidWarps * 256 * sizeof(uint32_t);
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(kMidThreads) k_rank_mid(const int64_t *rp, con
     extern __shared__ unsigned long long mid_sm[];
     unsigned long long *a = mid_sm, *b = mid_sm + kSortCap;
     uint32_t *cnt = reinterpret_cast<uint32_t *>(mid_sm + 2 * kSortCap);   // [warp][256] counts, then offsets
-    __shared__ uint32_t base[256];
+    __shared__ uint32_t wsum[kMidWarps];                                    // digit totals of 32-digit blocks
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t row = rows[blockIdx.x];
     const int64_t p0 = rp[row];
@@ -408,45 +410,43 @@ __global__ void __launch_bounds__(kMidThreads) k_rank_mid(const int64_t *rp, con
     for (int shift = 32; shift < 64; shift += 8) {
         for (int q = lane; q < 256; q += 32) cnt[warp * 256 + q] = 0;
         __syncwarp();
-        for (int c = s0; c < s1; c += 32) {                                       // per-warp digit counts
-            const int t = c + lane;
-            const int dg = t < s1 ? (int)((a[t] >> shift) & 0xff) : 256;
-            const unsigned peers = __match_any_sync(0xffffffffu, dg);
-            if (dg < 256 && (peers & lt_mask) == 0) cnt[warp * 256 + dg] += __popc(peers);
-            __syncwarp();
+        for (int t = s0 + lane; t < s1; t += 32) atomicAdd(cnt + warp * 256 + (int)((a[t] >> shift) & 0xff), 1u);
+        __syncthreads();
+        // thread q: digit q's total over warps; offsets digit-major, warp-minor
+        const int q = threadIdx.x;
+        uint32_t tot = 0;
+        for (int w = 0; w < kMidWarps; ++w) tot += cnt[w * 256 + q];
+        uint32_t inc = tot;                                                       // inclusive scan over this warp's digits
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        if (__syncthreads_or(tot == (uint32_t)d)) continue;                       // one digit holds all: order unchanged
+        uint32_t run = inc - tot;
+        for (int w = 0; w < warp; ++w) run += wsum[w];
+        for (int w = 0; w < kMidWarps; ++w) {
+            const uint32_t c2 = cnt[w * 256 + q];
+            cnt[w * 256 + q] = run;
+            run += c2;
         }
         __syncthreads();
-        int skip;
-        {   // thread q: digit q's total over warps, then offsets digit-major, warp-minor
-            const int q = threadIdx.x;
-            uint32_t tot = 0;
-            for (int w = 0; w < kMidWarps; ++w) tot += cnt[w * 256 + q];
-            base[q] = tot;
-            skip = __syncthreads_or(tot == (uint32_t)d);                          // one digit holds all
-            for (int o = 1; o < 256; o <<= 1) {                                  // inclusive scan of base
-                const uint32_t y = q >= o ? base[q - o] : 0u;
-                __syncthreads();
-                base[q] += y;
-                __syncthreads();
-            }
-            uint32_t run = base[q] - tot;                                         // exclusive
-            for (int w = 0; w < kMidWarps; ++w) {
-                const uint32_t c2 = cnt[w * 256 + q];
-                cnt[w * 256 + q] = run;
-                run += c2;
-            }
-        }
-        __syncthreads();
-        if (skip) continue;                                                       // the order is unchanged
-        for (int c = s0; c < s1; c += 32) {                                       // stable scatter
+        for (int c = s0; c < s1; c += 32) {                                       // stable scatter (warp-uniform loop)
             const int t = c + lane;
             const bool live = t < s1;
             const unsigned long long v = live ? a[t] : 0ull;
-            const int dg = live ? (int)((v >> shift) & 0xff) : 256;
-            const unsigned peers = __match_any_sync(0xffffffffu, dg);
-            if (live) b[cnt[warp * 256 + dg] + __popc(peers & lt_mask)] = v;
+            const uint32_t dg = live ? (uint32_t)((v >> shift) & 0xff) : 0u;
+            unsigned peers = __ballot_sync(0xffffffffu, live);
+#pragma unroll
+            for (int bit = 0; bit < 8; ++bit) {
+                const unsigned bb = __ballot_sync(0xffffffffu, (dg >> bit) & 1u);
+                peers &= ((dg >> bit) & 1u) ? bb : ~bb;
+            }
+            const uint32_t before = (uint32_t)__popc(peers & lt_mask);
+            if (live) b[cnt[warp * 256 + dg] + before] = v;
             __syncwarp();
-            if (live && (peers & lt_mask) == 0) cnt[warp * 256 + dg] += __popc(peers);
+            if (live && before == 0) cnt[warp * 256 + dg] += (uint32_t)__popc(peers);
             __syncwarp();
         }
         __syncthreads();
