@@ -85,6 +85,43 @@ def test_per_node_at_exponent_bit_exact(mode, e):
     np.testing.assert_array_equal(keep, ref)
 
 
+def boundary_graph(seed=8):
+    """Hubs of degree 512, 513, 1024, 4095, 4096 and 4097 -- the edges of the
+    per-row ranking classes (warp sort, CTA sort in shared memory, radix sort
+    of whole rows) -- over a sparse random background that avoids them."""
+    rng = np.random.default_rng(seed)
+    degs = (512, 513, 1024, 4095, 4096, 4097)
+    H, n = len(degs), 20000
+    u = [rng.integers(H, n, 30000)]
+    v = [rng.integers(H, n, 30000)]
+    for h, d in enumerate(degs):
+        u.append(np.full(d, h))
+        v.append(rng.choice(np.arange(H, n), d, replace=False))
+    return graphgen.from_edges(n, np.concatenate(u), np.concatenate(v)), degs
+
+
+@pytest.mark.parametrize("mode", ["local", "global"])
+@pytest.mark.parametrize("ties", [None, 3, 1])
+def test_rank_class_boundaries_bit_exact(mode, ties):
+    """Per-node selection at fixed exponents on rows at every class edge; with
+    one distinct score every row is a single tie run (each radix pass finds one
+    digit and is skipped), with three the runs span many warps."""
+    g, degs = boundary_graph()
+    assert tuple(int(x) for x in np.diff(g.row_ptr)[:len(degs)]) == degs
+    s = np.full(g.m, 0.5, np.float32) if ties == 1 else graphgen.random_scores(g.m, ties, seed=21)
+    L = lib()
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
+    try:
+        for e in (0.3, 0.6, 0.8, 0.95):
+            keep = np.zeros(g.m, np.uint8)
+            kept = L.ad_select_per_node(h, s, e, mode, keep)
+            ref, rk = oracle.select_per_node(g.row_ptr, g.col, s.astype(np.float64), mode, e)
+            assert kept == rk, (e, kept, rk)
+            np.testing.assert_array_equal(keep, ref)
+    finally:
+        L.ad_graph_destroy(h)
+
+
 def test_invalid_scores_rejected():
     L = lib()
     g = graphgen.grid2d(5, 5)
