@@ -348,7 +348,7 @@ def run_gpu(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if storage == "fp32" else "bf16 storage, f32 accumulate",
+                "vs_baseline": None, "dtype": "f32" if storage == "fp32" else f"{storage} storage, f32 accumulate",
                 "data": "synthetic",
                 "config": {"workload": workload(), "n": g.n, "n_active": n_active, "m": g.m, "nnz": g.nnz,
                            "R": R, "k": K_SWEEPS, "storage": storage, "graph_digest": g.digest(),
@@ -364,7 +364,11 @@ def run_gpu(args):
                 "roofline": {"kernel": "k_sweep (one JOR sweep + fused rescale min/max)", "bound": "hbm",
                              "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                              "peak_kind": peak_kind, "algorithmic_bytes_per_launch": b_sweep,
-                             "avg_launch_ms": sweep_ms, "traffic": sweep_traffic(storage)},
+                             "avg_launch_ms": sweep_ms, "traffic": sweep_traffic(storage),
+                             # not roofline terms: every CSR entry gathers one R-wide neighbour row, which
+                             # the L1/L2 serve; this is the rate the sweep sustains on those gathers
+                             "gathered_bytes_per_launch": g.nnz * R * (4 if storage == "fp32" else 2),
+                             "gather_rate_gbs": g.nnz * R * (4 if storage == "fp32" else 2) / (sweep_ms / 1e3) / 1e9},
                 "gpu_launches": int(launches),
                 "storage_variants": variants or None,
                 "sparsify_binned": binned,
