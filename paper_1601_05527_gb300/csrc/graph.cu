@@ -162,43 +162,92 @@ __global__ void k_check_entries(const int64_t *rp, const int32_t *col, const flo
     }
 }
 
+// Fast validation pass over valid-looking input: the same per-entry checks, but
+// each undirected pair is looked up once -- by the entry of the longer row
+// (equal lengths: of the larger row id), in the shorter row -- and that thread
+// records both mirror positions.  Found partners are distinct entries of the
+// other kind, so with no violation reported, 2 * pairs == nnz means every entry
+// has its mirror; otherwise the caller reruns k_check_entries for the report.
+__global__ void k_check_pairs(const int64_t *rp, const int32_t *col, const float *w, const int32_t *erow, int64_t n,
+                              int64_t nnz, const int64_t *voff, int32_t G, unsigned long long *err,
+                              unsigned long long *pairs, int64_t *mirror) {
+    unsigned long long found = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = erow[p];
+        const int32_t j = col[p];
+        if (j < 0 || j >= n) { report(err, P_CSR, p); continue; }
+        if (j == i) { report(err, P_SELF, p); continue; }
+        if (p > rp[i] && col[p - 1] >= j) { report(err, P_DUP, p); continue; }
+        if (w) {
+            const float x = w[p];
+            if (!(x > 0.f) || !isfinite(x)) { report(err, P_WEIGHT, p); continue; }
+        }
+        if (G > 1) {
+            int lo = 0, hi = G;
+            while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (voff[mid] <= i) lo = mid; else hi = mid; }
+            if (j < voff[lo] || j >= voff[lo + 1]) { report(err, P_BATCH, p); continue; }
+        }
+        const int64_t di = rp[i + 1] - rp[i], dj = rp[j + 1] - rp[j];
+        if (!(dj < di || (dj == di && j < i))) continue;     // the pair's other entry looks it up
+        const int64_t q = find_in_row(rp, col, j, (int32_t)i);
+        if (q < 0) { report(err, P_SYM, p); continue; }
+        if (w && __float_as_uint(w[q]) != __float_as_uint(w[p])) report(err, P_SYM, p < q ? p : q);
+        mirror[p] = q;
+        mirror[q] = p;
+        ++found;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);
+    if ((threadIdx.x & 31) == 0 && found) atomicAdd(pairs, found);
+}
+
 // ----------------------------------------------------------------------------
 // Degrees and edge numbering
 // ----------------------------------------------------------------------------
+// First upper entry of every row (rows are sorted), and D, D^-1 for unit
+// weights: one thread per row, so that the binary searches of many rows are in
+// flight at once.
 __global__ void k_degrees(const int64_t *rp, const int32_t *col, const float *w, int64_t n, double *D, float *Dinv,
                           int64_t *upos, int64_t *ucount) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        int64_t lo = b, hi = e;   // first position with col > i
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (col[mid] <= i) lo = mid + 1; else hi = mid;
+        }
+        upos[i] = lo;
+        ucount[i] = e - lo;
+        if (!w) {
+            const double s = (double)(e - b);
+            D[i] = s;
+            Dinv[i] = s > 0.0 ? (float)(1.0 / s) : 0.f;
+        }
+    }
+}
+
+// weighted degrees D_i = sum_j w_ij in FP64: a warp per row, lanes strided over
+// the row in a fixed order
+__global__ void k_wdegrees(const int64_t *rp, const float *w, int64_t n, double *D, float *Dinv) {
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W) {
         const int64_t b = rp[i], e = rp[i + 1];
-        double s;
-        if (w) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four independent loads in flight per lane
-            int64_t p = b + lane;
-            for (; p + 96 < e; p += 128) {
-                s0 += (double)w[p];
-                s1 += (double)w[p + 32];
-                s2 += (double)w[p + 64];
-                s3 += (double)w[p + 96];
-            }
-            for (; p < e; p += 32) s0 += (double)w[p];
-            s = (s0 + s1) + (s2 + s3);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        } else {
-            s = (double)(e - b);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four independent loads in flight per lane
+        int64_t p = b + lane;
+        for (; p + 96 < e; p += 128) {
+            s0 += (double)w[p];
+            s1 += (double)w[p + 32];
+            s2 += (double)w[p + 64];
+            s3 += (double)w[p + 96];
         }
+        for (; p < e; p += 32) s0 += (double)w[p];
+        double s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
-            // first position with col > i (rows are sorted)
-            int64_t lo = b, hi = e;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (col[mid] <= i) lo = mid + 1; else hi = mid;
-            }
             D[i] = s;
             Dinv[i] = s > 0.0 ? (float)(1.0 / s) : 0.f;
-            upos[i] = lo;
-            ucount[i] = e - lo;
         }
     }
 }
@@ -207,8 +256,15 @@ __global__ void k_degrees(const int64_t *rp, const int32_t *col, const float *w,
 __global__ void k_entry_rows(const int64_t *rp, int64_t n, int32_t *erow) {
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W)
-        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) erow[p] = (int32_t)i;
+    // 32 rows per warp and round: their bounds are loaded at once, then written row by row
+    for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n; base += W * 32) {
+        const int64_t i = base + lane;
+        const long long b = i < n ? rp[i] : 0, e = i < n ? rp[i + 1] : 0;
+        for (int r = 0; r < 32; ++r) {
+            const long long br = __shfl_sync(0xffffffffu, b, r), er = __shfl_sync(0xffffffffu, e, r);
+            for (long long p = br + lane; p < er; p += 32) erow[p] = (int32_t)(base + r);
+        }
+    }
 }
 
 // one thread per entry: position of the reverse entry (binary search in row col[p])
@@ -279,9 +335,13 @@ static ad_status compute_anchors(ad_graph_t g) {
 ad_status recompute_degrees(ad_graph_t g) {
     int64_t *ucount = nullptr;
     AD_TRY(dalloc_t(g, g->n + 1, &ucount));
-    const int64_t blocks = std::min<int64_t>((g->n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
-    AD_LAUNCH(k_degrees, (int)blocks, 256, 0, g->stream, g->rp, g->col, g->w, g->n, g->D, g->Dinv, g->upos,
+    const int64_t tblocks = std::min<int64_t>((g->n + 255) / 256 + 1, (int64_t)g->num_sms * 16);
+    AD_LAUNCH(k_degrees, (int)tblocks, 256, 0, g->stream, g->rp, g->col, g->w, g->n, g->D, g->Dinv, g->upos,
               ucount);
+    if (g->w) {
+        const int64_t wblocks = std::min<int64_t>((g->n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
+        AD_LAUNCH(k_wdegrees, (int)wblocks, 256, 0, g->stream, g->rp, g->w, g->n, g->D, g->Dinv);
+    }
     int64_t m = 0;
     ad_status st = exclusive_scan_i64(g, ucount, g->eoff, g->n, &m);
     dfree(g, ucount);
@@ -310,10 +370,10 @@ __global__ void k_pick_i64(const int64_t *src, const int64_t *idx, int64_t count
 
 ad_status graph_setup(ad_graph_t g, int32_t flags) {
     const int64_t n = g->n;
-    unsigned long long *err = nullptr;
-    AD_TRY(dalloc_t(g, 2, &err));
+    unsigned long long *err = nullptr;   // [0] first violation, [1] active rows, [2] pairs found
+    AD_TRY(dalloc_t(g, 3, &err));
     AD_CUDA_TRY(cudaMemsetAsync(err, 0xff, sizeof(unsigned long long), g->stream));
-    AD_CUDA_TRY(cudaMemsetAsync(err + 1, 0, sizeof(unsigned long long), g->stream));
+    AD_CUDA_TRY(cudaMemsetAsync(err + 1, 0, 2 * sizeof(unsigned long long), g->stream));
     const int grid = g->num_sms * 8;
     if (!(flags & AD_CREATE_SKIP_VALIDATION)) {
         AD_LAUNCH(k_check_rows, grid, 256, 0, g->stream, g->rp, n, g->nnz, err);
@@ -322,10 +382,18 @@ ad_status graph_setup(ad_graph_t g, int32_t flags) {
         if (e0 == ~0ull && g->nnz > 0) {   // row pointers are sound: row ids, then the entries
             AD_TRY(dalloc_t(g, g->nnz, &g->erow));
             AD_TRY(dalloc_t(g, g->nnz, &g->mirror));
-            const int64_t wblocks = std::min<int64_t>((n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
+            const int64_t wblocks = std::min<int64_t>((n + 255) / 256 + 1, (int64_t)g->num_sms * 16);
             AD_LAUNCH(k_entry_rows, (int)wblocks, 256, 0, g->stream, g->rp, n, g->erow);
-            AD_LAUNCH(k_check_entries, g->num_sms * 16, 256, 0, g->stream, g->rp, g->col, g->w, g->erow, n, g->nnz,
-                      g->voff, g->G, err, g->mirror);
+            AD_LAUNCH(k_check_pairs, g->num_sms * 16, 256, 0, g->stream, g->rp, g->col, g->w, g->erow, n, g->nnz,
+                      g->voff, g->G, err, err + 2, g->mirror);
+            unsigned long long fast[3] = {0, 0, 0};
+            AD_TRY(copy_out(g, fast, err, sizeof(fast)));
+            if (fast[0] != ~0ull || 2 * fast[2] != (unsigned long long)g->nnz) {
+                // a violation: the per-entry pass reports the first one by priority and position
+                AD_CUDA_TRY(cudaMemsetAsync(err, 0xff, sizeof(unsigned long long), g->stream));
+                AD_LAUNCH(k_check_entries, g->num_sms * 16, 256, 0, g->stream, g->rp, g->col, g->w, g->erow, n,
+                          g->nnz, g->voff, g->G, err, g->mirror);
+            }
         }
         AD_TRY(copy_out(g, &e0, err, sizeof(e0)));
         if (e0 != ~0ull) {
@@ -361,7 +429,7 @@ ad_status ensure_mirror(ad_graph_t g) {
     if (!g->mirror) {   // not recorded by validation (handles created without it)
         AD_TRY(dalloc_t(g, g->nnz, &g->erow));
         AD_TRY(dalloc_t(g, g->nnz, &g->mirror));
-        const int64_t wblocks = std::min<int64_t>((g->n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
+        const int64_t wblocks = std::min<int64_t>((g->n + 255) / 256 + 1, (int64_t)g->num_sms * 16);
         AD_LAUNCH(k_entry_rows, (int)wblocks, 256, 0, g->stream, g->rp, g->n, g->erow);
         AD_LAUNCH(k_mirror, grid, 256, 0, g->stream, g->rp, g->col, g->erow, g->nnz, g->mirror);
     }
