@@ -114,3 +114,64 @@ def test_fit_is_the_brute_force_union():
         if e > 2.0 ** -40:
             assert union(e - 2.0 ** -40).sum() < K
     assert oracle.sparsify_binned(g.row_ptr, g.col, scores, 9, 1.0)[1] == g.m
+
+
+def expected_bins(scores, d):
+    """floor((x - min) / h), h = 3.5 sigma / d^(1/3) with the population sigma."""
+    sigma = float(np.std(scores))                      # population (divides by d)
+    h = 3.5 * sigma / d ** (1.0 / 3.0)
+    frac = (scores - scores.min()) / h
+    nz = frac[frac > 0]
+    assert np.min(np.abs(nz - np.round(nz))) > 1e-3    # no value near a bin edge
+    return np.floor(frac).astype(np.int64)
+
+
+def test_bins_measure_from_the_smallest_distance():
+    """The same progression shifted away from 0: bins count from the row minimum."""
+    d = 64
+    g = star(d)
+    scores = 0.37 + np.arange(d, dtype=np.float64) / 64
+    _, bins = oracle.binned_ranks(g.row_ptr, g.col, scores, seed=5, return_bins=True)
+    np.testing.assert_array_equal(bins[:d], expected_bins(scores, d))
+
+
+def test_bins_use_the_population_sigma():
+    """d = 12 equally spaced distances: the sample sigma (divide by d - 1) would
+    move one value into the next bin; the population sigma is the rule's."""
+    d = 12
+    g = star(d)
+    scores = np.arange(d, dtype=np.float64) / 16
+    _, bins = oracle.binned_ranks(g.row_ptr, g.col, scores, seed=5, return_bins=True)
+    expect = expected_bins(scores, d)
+    sample = np.floor((scores - scores.min()) / (3.5 * np.std(scores, ddof=1) / d ** (1.0 / 3.0)))
+    assert (sample != expect).any()                    # the case tells the two apart
+    np.testing.assert_array_equal(bins[:d], expect)
+
+
+def bin_word(seed, i, b):
+    return int(oracle.philox4x32_10([i & 0xFFFFFFFF, i >> 32, 1 + b, BIN_STREAM], [seed & 0xFFFFFFFF, seed >> 32])[0])
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_bins_of_a_round_follow_their_random_words(seed):
+    """Within a round the bins give their entries in ascending Philox word of
+    (vertex, 1 + bin) -- the random order of the bins."""
+    g = graphgen.rmat(9, 12, seed=seed)
+    scores = graphgen.random_scores(g.m, None, seed=seed).astype(np.float64) ** 3
+    rank, bins = oracle.binned_ranks(g.row_ptr, g.col, scores, seed=seed, return_bins=True)
+    checked = 0
+    for i in range(g.n):
+        p0, p1 = g.row_ptr[i], g.row_ptr[i + 1]
+        bn = bins[p0:p1]
+        if len(set(bn.tolist())) < 2:
+            continue
+        seq = bn[np.argsort(rank[p0:p1])]              # bins in selection order
+        taken, rounds = {}, {}
+        for b in seq.tolist():
+            taken[b] = taken.get(b, 0) + 1
+            rounds.setdefault(taken[b], []).append(b)
+        for r, bs in rounds.items():
+            words = [bin_word(seed, i, b) for b in bs]
+            assert words == sorted(words), (i, r, bs)
+        checked += 1
+    assert checked > 20

@@ -6,7 +6,11 @@
   * P: the argmax of Eq. (P) on a dense matrix of delta = 1/rho;
   * Galerkin: P^T L_f P computed densely equals the Laplacian of the coarse CSR;
   * uncoarsening: brute force over fine edges;
-  * the level-span ratio vectors of the paper's 6-level example (golden);
+  * the level-span ratio vectors of the paper's 6-level example (golden), and
+    the reading for an odd remainder;
+  * the stall guard on disjoint triangles, which keep 2/3 of their vertices;
+  * Alg. 6 on two levels rebuilt from its steps (Philox streams of the way
+    down and up, ratio order);
   * the fitted keep fraction is the smallest 2^-20 grid point reaching K.
 """
 import json
@@ -162,3 +166,60 @@ def test_hierarchy_and_target_fraction():
     keep_f, kept_f, _ = ml.sparsify(ratios)
     assert kept_f == keep_f.sum() >= oracle.target_count(g.m, 0.5)
     ml.close()
+
+
+def test_middle_segment_of_an_odd_remainder():
+    """The paper's example has L - level_span even.  Reading for an odd
+    remainder: the middle segment starts floor((L - span) / 2) levels from the
+    coarsest, i.e. it leans coarse."""
+    np.testing.assert_array_equal(oracle.segment_ratios(5, "middle", 2, 0.3), [-1, 0.3, 0.3, -1, -1])
+    np.testing.assert_array_equal(oracle.segment_ratios(7, "middle", 2, 0.3), [-1, -1, 0.3, 0.3, -1, -1, -1])
+
+
+def triangles(T):
+    u = np.concatenate([3 * np.arange(T), 3 * np.arange(T), 3 * np.arange(T) + 1])
+    v = np.concatenate([3 * np.arange(T) + 1, 3 * np.arange(T) + 2, 3 * np.arange(T) + 2])
+    return graphgen.from_edges(3 * T, u, v)
+
+
+def test_triangles_coarsen_by_two_thirds():
+    """In a unit-weight triangle the first vertex is a seed, the second one too
+    (its weight to seeds, 1, is <= Q D = 1), the third not (2 > 1): each level
+    keeps 2/3 of the vertices, which the stall guard (n_c > 0.9 n_f) accepts."""
+    T = 50
+    g = triangles(T)
+    seeds = oracle.create_seeds(g.row_ptr, g.col, None, Q=0.5)
+    assert seeds.reshape(T, 3).tolist() == [[1, 1, 0]] * T
+    ml = oracle.Multilevel(g.row_ptr, g.col, None, R=4, k=5, omega=0.5, seed=3, coarsest_n=10)
+    assert ml.levels >= 2
+    assert ml.level_size(1) == (2 * T, T)          # one coarse edge per triangle
+    ml.close()
+
+
+@pytest.mark.parametrize("mode", ["local", "global"])
+def test_two_levels_compose_the_steps_of_alg6(mode):
+    """A two-level hierarchy against Alg. 6 rebuilt from its steps: distances on
+    the way down use Philox stream 2l, the recomputed ones on the way up 2l + 1;
+    ratios[0] belongs to the coarsest level."""
+    g = weighted_ba(400, 4, 11)
+    w = g.weight.astype(np.float64)
+    R, k, om, seed, f = 8, 10, 0.5, 21, 0.4
+    ml = oracle.Multilevel(g.row_ptr, g.col, w, R=R, k=k, omega=om, seed=seed, max_levels=2, coarsest_n=1,
+                           mode=mode)
+    assert ml.levels == 2
+    rho0 = oracle.algebraic_distance(g.row_ptr, g.col, w, R=R, k=k, omega=om, seed=seed, stream=0)
+    agg, nc = oracle.aggregate(g.row_ptr, g.col, rho0, oracle.create_seeds(g.row_ptr, g.col, w, Q=0.5))
+    rpc, cic, wc, f2c = oracle.galerkin(g.row_ptr, g.col, w, agg, nc)
+    assert ml.level_size(1) == (nc, len(cic) // 2)
+    # coarsest level only: select on the coarse graph, then uncoarsen
+    rho1 = oracle.algebraic_distance(rpc, cic, wc, R=R, k=k, omega=om, seed=seed, stream=2)
+    keep_c, _, _ = oracle.sparsify(rpc, cic, rho1, mode, "per_node", f)
+    keep, _, _ = ml.sparsify([f, -1.0])
+    np.testing.assert_array_equal(keep, oracle.uncoarsen(f2c, keep_c))
+    # finest level only: every edge survives the coarse level, distances are recomputed
+    rho0_up = oracle.algebraic_distance(g.row_ptr, g.col, w, R=R, k=k, omega=om, seed=seed, stream=1)
+    keep_f, _, _ = oracle.sparsify(g.row_ptr, g.col, rho0_up, mode, "per_node", f)
+    keep, _, _ = ml.sparsify([-1.0, f])
+    np.testing.assert_array_equal(keep, keep_f)
+    ml.close()
+

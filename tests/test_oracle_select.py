@@ -133,3 +133,12 @@ def test_strong_and_weak_selection_on_planted_clusters():
     K = int(cut.sum())
     assert np.all(oracle.select_whole_graph(rho, "global", K) == cut)
     assert np.all(oracle.select_whole_graph(rho, "local", g.m - K) == 1 - cut)
+
+
+def test_target_count_is_the_nearest_integer():
+    """K = floor(f m + 1/2): the integer nearest to f m, halves rounding up."""
+    cases = [(10, 0.25, 3), (10, 0.24, 2), (10, 0.26, 3), (7, 0.5, 4), (3, 1 / 3, 1), (100, 0.304, 30),
+             (100, 0.306, 31), (0, 0.5, 0), (57, 0.0, 0), (57, 1.0, 57)]
+    for m, f, K in cases:
+        assert oracle.target_count(m, f) == K, (m, f)
+
