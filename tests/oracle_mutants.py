@@ -6,10 +6,12 @@ rebuilds the oracle and runs the CPU suite (pytest -m "not gpu").  A mistake
 that no test catches marks a weak pin.  The source is restored (and the oracle
 rebuilt) after every mutant and on any exit.
 
-Two mutants are equivalent and are expected to survive:
+Three mutants are equivalent and are expected to survive:
   target_min0  the clamp T >= 1 never acts: d >= 1 and e >= 0 give d^e >= 1;
   grad_A_sign  the rescale term it changes is multiplied by sum_i dL/dx_i, which
-               is zero for a loss of distances (shifting every x leaves L unchanged).
+               is zero for a loss of distances (shifting every x leaves L unchanged);
+  upward_rescale_once  rescaling once after the sweeps equals rescaling after
+               every sweep in exact arithmetic (the sweep commutes with affine maps).
 """
 import os
 import shutil
@@ -19,7 +21,7 @@ import tempfile
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, 'oracle', 'ad_oracle.c')
-EQUIVALENT = {'target_min0', 'grad_A_sign'}
+EQUIVALENT = {'target_min0', 'grad_A_sign', 'upward_rescale_once'}
 
 M = [
     # Philox and init
@@ -91,6 +93,20 @@ M = [
     ('grad_drop_avg', 'gentry[p] += ybar[i] * omega * (xp[ci[p]] - avg) / D[i];', 'gentry[p] += ybar[i] * omega * (xp[ci[p]]) / D[i];', 0),
     ('grad_alpha_omega', 'xbar[j] = alpha * ybar[j] + s;', 'xbar[j] = omega * ybar[j] + s;', 0),
     ('grad_transposed_D', 's += ybar[i] * omega * (w ? w[p] : 1.0) / D[i];', 's += ybar[i] * omega * (w ? w[p] : 1.0) / D[j];', 0),
+    # second batch: Galerkin, kept subgraph, upward pass, fit, Local Degree key, init layout
+    ('galerkin_not_canonical', 'pairs[np].a = I < J ? I : J; pairs[np].b = I < J ? J : I;', 'pairs[np].a = I; pairs[np].b = J;', 0),
+    ('galerkin_drops_w', 'pairs[np].fe = e; pairs[np].w = w ? w[p] : 1.0; ++np;', 'pairs[np].fe = e; pairs[np].w = 1.0; ++np;', 0),
+    ('kept_subgraph_drops_w', 'ci_s[q] = ci[p]; w_s[q] = w ? w[p] : 1.0; ++q;', 'ci_s[q] = ci[p]; w_s[q] = 1.0; ++q;', 0),
+    ('coarsest_starts_empty', 'for (int64_t e = 0; e < v->m; ++e) keep[e] = 1;', 'for (int64_t e = 0; e < v->m; ++e) keep[e] = 0;', 0),
+    ('levels_stop_strict', 'if (cn <= coarsest_n || l + 1 >= max_levels) break;', 'if (cn < coarsest_n || l + 1 >= max_levels) break;', 0),
+    ('ml_fit_19_halvings', 'for (int it = 0; it < 20; ++it) {', 'for (int it = 0; it < 19; ++it) {', 0),
+    ('alg2_returns_lo', '    *n_kept = union_of_tops(n, rp, sorted_e, m, hi, keep);\n    *e_used = hi;\n    free(sorted_e);', '    *n_kept = union_of_tops(n, rp, sorted_e, m, lo, keep);\n    *e_used = lo;\n    free(sorted_e);', 0),
+    ('ld_key_is_id', 'a[t].d = rp[j + 1] - rp[j];', 'a[t].d = j;', 0),
+    ('init_layout_transposed', 'x[i * R + r] = orc_test_value(seed, stream, i, r);', 'x[r * n + i] = orc_test_value(seed, stream, i, r);', 0),
+    ('whole_graph_mode_swapped', 'qsort(a, (size_t)m, sizeof(scored_edge), mode ? cmp_descending : cmp_ascending);', 'qsort(a, (size_t)m, sizeof(scored_edge), mode ? cmp_ascending : cmp_descending);', 0),
+    ('normalize_divides', 'if (normalize) s *= sqrt(D[i] * D[ci[p]]);', 'if (normalize) s /= sqrt(D[i] * D[ci[p]]);', 0),
+    ('upward_rescale_once', '(uint32_t)(2 * l + 1), 0, 0, NULL, NULL, rhos)', '(uint32_t)(2 * l + 1), 1, 0, NULL, NULL, rhos)', 0),
+    ('seed_numbering_all', 'for (int64_t i = 0; i < n; ++i) agg[i] = is_seed[i] ? (int32_t)(nc++) : -1;', 'for (int64_t i = n - 1; i >= 0; --i) agg[i] = is_seed[i] ? (int32_t)(nc++) : -1;', 0),
 ]
 
 

@@ -194,6 +194,11 @@ def test_triangles_coarsen_by_two_thirds():
     assert ml.levels >= 2
     assert ml.level_size(1) == (2 * T, T)          # one coarse edge per triangle
     ml.close()
+    # a level of exactly coarsest_n vertices is small enough: the hierarchy stops there
+    for cn, more in ((3 * T, False), (3 * T - 1, True)):
+        ml = oracle.Multilevel(g.row_ptr, g.col, None, R=4, k=5, omega=0.5, seed=3, coarsest_n=cn)
+        assert (ml.levels > 1) == more, cn
+        ml.close()
 
 
 @pytest.mark.parametrize("mode", ["local", "global"])
