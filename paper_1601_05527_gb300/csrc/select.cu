@@ -976,8 +976,9 @@ ad_status select_whole_graph(ad_graph_t g, const float *score, double fraction, 
 }
 
 // Ranks of every CSR entry inside its row by (ekey, position), ascending, in
-// both orders (RankOut), by degree class: register counting, warp and CTA
-// bitonic sorts, and the radix sort for rows above the CTA sort's capacity.
+// both orders (RankOut), by degree class: register counting, warp bitonic
+// sorts, a CTA radix sort in shared memory, and the device radix sort for rows
+// above the CTA sort's capacity.
 static ad_status entry_ranks(ad_graph_t g, ad_graph_s::SelCache *c, const uint32_t *ekey, RankOut out) {
     auto wblocks = [&](int64_t rows_, int per_warp) {
         return (int)std::max<int64_t>(1, std::min<int64_t>((rows_ + 8 * per_warp - 1) / (8 * per_warp),
