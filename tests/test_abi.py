@@ -62,3 +62,26 @@ def test_argument_errors_without_device_work(lib):
     assert "segment" in _lib.ad_last_error()
     with pytest.raises(_lib.ADError):
         _lib.ad_graph_create(-1, np.zeros(1, np.int64), np.zeros(0, np.int32))
+
+
+def test_entry_points_fail_loudly_without_the_library():
+    """No CPU fallback: with libad.so absent every entry point raises instead of
+    computing anything (run in a fresh process, where nothing is loaded yet)."""
+    import subprocess
+    import sys
+    code = (
+        "import os, numpy as np\n"
+        "real = os.path.exists\n"
+        "os.path.exists = lambda p: False if str(p).endswith('libad.so') else real(p)\n"
+        "from paper_1601_05527_gb300 import _lib as L\n"
+        "for call in (lambda: L.ad_graph_create(2, np.array([0, 1, 2]), np.array([1, 0], np.int32), None),\n"
+        "             lambda: L.ad_version(), lambda: L.load()):\n"
+        "    try:\n"
+        "        call()\n"
+        "        print('computed')\n"
+        "    except ImportError as e:\n"
+        "        print('raised:', e)\n"
+    )
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    lines = r.stdout.strip().splitlines()
+    assert len(lines) == 3 and all(l.startswith("raised:") and "missing" in l for l in lines), r.stdout + r.stderr
