@@ -45,7 +45,9 @@
  *       the upper end, the smallest grid point whose kept count is >= K.
  *   R9  Seeds (Sec. 5 "The Coarsening"): visit active vertices by decreasing
  *       weighted degree (ties: smaller id first) and move i to C when the
- *       weight from i to the seeds chosen so far is <= Q * D_i.
+ *       weight from i to the seeds chosen so far is <= Q * D_i.  The paper
+ *       states no coupling rule, so parity with its own hierarchy is
+ *       unpinned; this rule is pinned by the condition that determines it.
  *   R10 Eq. (P): an F vertex joins the seed neighbour of largest delta, that
  *       is smallest rho; ties go to the smaller seed id.  Coarse ids number
  *       the seeds by increasing vertex id.
@@ -56,7 +58,9 @@
  *       level, -1 means no sparsification at that level, otherwise the value
  *       is the fraction of that level's current edges to keep, met by fitting
  *       e with the bisection of R8.  Philox stream of level l is 2l on
- *       the way down and 2l+1 for the recomputation on the way up.
+ *       the way down and 2l+1 for the recomputation on the way up.  A span
+ *       of levels in the middle of L levels starts floor((L - span) / 2)
+ *       levels from the coarsest (the paper's example has L - span even).
  *   R13 SparsifyB (Alg. 3; its text stops mid-sentence).  Per node, sigma is
  *       the population standard deviation of its incident distances; the bin
  *       width is h = 3.5 sigma / cbrt(d) and the bin of a distance is
@@ -71,6 +75,13 @@
  *       and bins are computed in FP32 (distances are FP32 values), sums
  *       sequentially in CSR order, cbrt(d) as FP64 cbrt rounded to FP32.  Union
  *       over the two ends of an edge and the fit of e are those of Alg. 2 (R8).
+ *   R14 Local Degree (the comparison method of Sec. 1.1 and Sec. 6): node i
+ *       ranks its neighbours by their degree, largest first, ties by CSR
+ *       position (smaller id first), and keeps the first T(d_i, e) (R7);
+ *       union and fit of e as Alg. 2 (R8).
+ *   R15 Reverse mode: L = sum over a subset S of rho_e^2 through the
+ *       per-sweep form; the min and max of each rescale take their
+ *       sub-gradient at the lowest-index argmin / argmax.
  */
 #include <stdint.h>
 #include <stdlib.h>
