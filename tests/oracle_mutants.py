@@ -1,6 +1,7 @@
 """Mutation sweep of the C oracle (run by hand: python tests/oracle_mutants.py).
 
-Each entry plants one plausible mistake in oracle/ad_oracle.c -- a swapped
+Each entry plants one plausible mistake in oracle/ad_oracle.c (or in the
+argument conversions of its Python binding, oracle/__init__.py) -- a swapped
 operand, a dropped term, a wrong index, sign or constant, an off-by-one -- then
 rebuilds the oracle and runs the CPU suite (pytest -m "not gpu").  A mistake
 that no test catches marks a weak pin.  The source is restored (and the oracle
@@ -21,6 +22,7 @@ import tempfile
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, 'oracle', 'ad_oracle.c')
+PY_SRC = os.path.join(ROOT, 'oracle', '__init__.py')
 EQUIVALENT = {'target_min0', 'grad_A_sign', 'upward_rescale_once'}
 
 M = [
@@ -111,6 +113,17 @@ M = [
 
 
 
+# mistakes in the Python binding of the oracle (argument conversions)
+PY_M = [
+    ('py_alpha_not_converted', 'R, k, 1.0 - omega,\n                                     seed, stream, mode,', 'R, k, omega,\n                                     seed, stream, mode,', 0),
+    ('py_ml_alpha_not_converted', 'R, k, 1.0 - omega, seed, Q, coarsest_n,', 'R, k, omega, seed, Q, coarsest_n,', 0),
+    ('py_grad_alpha_not_converted', 'R, k, 1.0 - omega, seed,\n                            stream,', 'R, k, omega, seed,\n                            stream,', 0),
+    ('py_modes_swapped', 'MODES = {"local": 0, "global": 1}', 'MODES = {"local": 1, "global": 0}', 0),
+    ('py_scopes_swapped', 'SCOPES = {"per_node": 0, "whole_graph": 1}', 'SCOPES = {"per_node": 1, "whole_graph": 0}', 0),
+    ('py_rescale_modes_swapped', 'mode = {"per_sweep": 0, "end": 1}[rescale]', 'mode = {"per_sweep": 1, "end": 0}[rescale]', 0),
+]
+
+
 def nth_replace(s, old, new, k):
     idx = -1
     for _ in range(k + 1):
@@ -132,7 +145,24 @@ def main():
     backup = os.path.join(tempfile.mkdtemp(prefix='oracle_mutants_'), 'ad_oracle.c')
     shutil.copy(SRC, backup)
     res = {}
+    py_orig = open(PY_SRC).read()
     try:
+        for name, old, new, k in PY_M:
+            if only and name not in only:
+                continue
+            if py_orig.count(old) <= k:
+                res[name] = 'pattern missing'
+                print(name, res[name], flush=True)
+                continue
+            with open(PY_SRC, 'w') as f:
+                f.write(nth_replace(py_orig, old, new, k))
+            r = subprocess.run([sys.executable, '-m', 'pytest', 'tests', '-m', 'not gpu', '-x', '-q',
+                                '-p', 'no:cacheprovider'], cwd=ROOT, capture_output=True, text=True, timeout=900)
+            with open(PY_SRC, 'w') as f:
+                f.write(py_orig)
+            res[name] = 'killed' if r.returncode != 0 else 'survived'
+            first = [l for l in r.stdout.splitlines() if l.startswith('FAILED')][:1]
+            print(name, res[name], first[0][:110] if first else '', flush=True)
         for name, old, new, k in M:
             if only and name not in only:
                 continue
@@ -153,6 +183,8 @@ def main():
             first = [l for l in r.stdout.splitlines() if l.startswith('FAILED')][:1]
             print(name, res[name], first[0][:110] if first else '', flush=True)
     finally:
+        with open(PY_SRC, 'w') as f:
+            f.write(py_orig)
         with open(SRC, 'w') as f:
             f.write(orig)
         rebuild()

@@ -201,14 +201,14 @@ def test_triangles_coarsen_by_two_thirds():
         ml.close()
 
 
-@pytest.mark.parametrize("mode", ["local", "global"])
-def test_two_levels_compose_the_steps_of_alg6(mode):
+@pytest.mark.parametrize("mode,om", [("local", 0.5), ("global", 0.5), ("local", 0.35)])
+def test_two_levels_compose_the_steps_of_alg6(mode, om):
     """A two-level hierarchy against Alg. 6 rebuilt from its steps: distances on
     the way down use Philox stream 2l, the recomputed ones on the way up 2l + 1;
     ratios[0] belongs to the coarsest level."""
     g = weighted_ba(400, 4, 11)
     w = g.weight.astype(np.float64)
-    R, k, om, seed, f = 8, 10, 0.5, 21, 0.4
+    R, k, seed, f = 8, 10, 21, 0.4
     ml = oracle.Multilevel(g.row_ptr, g.col, w, R=R, k=k, omega=om, seed=seed, max_levels=2, coarsest_n=1,
                            mode=mode)
     assert ml.levels == 2
