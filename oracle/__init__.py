@@ -34,11 +34,14 @@ F64P = ctypes.POINTER(ctypes.c_double)
 
 
 def build(force: bool = False) -> str:
-    """Compile ad_oracle.c into liboracle.so (plain gcc, no target-specific flags)."""
+    """Compile ad_oracle.c into liboracle.so (plain gcc, no target-specific flags),
+    with OpenMP where the compiler has it (the row loops of Alg. 1 then run on
+    several host threads, with results that do not depend on the thread count)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-Wall", "-Wextra", _SRC, "-o", tmp, "-lm"])
+        base = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-Wextra"]
+        if subprocess.call(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base + [_SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -51,6 +54,9 @@ def _L():
             lib = ctypes.CDLL(_LIB_PATH)
             sig = {
                 "orc_philox4x32_10": (None, [U32P, U32P, U32P]),
+                "orc_set_threads": (None, [ctypes.c_int32]),
+                "orc_max_threads": (ctypes.c_int32, []),
+                "orc_last_phase_seconds": (None, [F64P]),
                 "orc_test_value": (ctypes.c_double, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int32]),
                 "orc_init_vectors": (None, [ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, F64P]),
                 "orc_count_edges": (ctypes.c_int64, [ctypes.c_int64, I64P, I32P]),
@@ -108,6 +114,23 @@ def _csr(rp, ci, w=None):
     ci = np.ascontiguousarray(ci, dtype=np.int32)
     w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
     return rp, ci, w
+
+
+# --------------------------------------------------------------------------- threads
+def set_threads(n: int):
+    """Host threads of the oracle's row loops (1 = sequential)."""
+    _L().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_L().orc_max_threads())
+
+
+def last_phase_seconds():
+    """(init, sweeps, distance) wall seconds of the last algebraic_distance call."""
+    out = np.zeros(3, dtype=np.float64)
+    _L().orc_last_phase_seconds(_p(out, F64P))
+    return {"init": float(out[0]), "sweeps": float(out[1]), "distance": float(out[2])}
 
 
 # --------------------------------------------------------------------------- Philox / init

@@ -71,9 +71,8 @@
  *       contributes before any contributes twice.  Random order = ascending
  *       word 0 of Philox4x32-10 with key = the selection seed and counter
  *       (edge id lo, hi, 0, 0xB1000000) for an entry, (vertex lo, hi, 1 + bin,
- *       0xB1000000) for a bin; ties by position / bin index.  The statistics
- *       and bins are computed in FP32 (distances are FP32 values), sums
- *       sequentially in CSR order, cbrt(d) as FP64 cbrt rounded to FP32.  Union
+ *       0xB1000000) for a bin; ties by position / bin index.  Mean, sigma,
+ *       h and the bin index are FP64, sums sequential in CSR order.  Union
  *       over the two ends of an edge and the fit of e are those of Alg. 2 (R8).
  *   R14 Local Degree (the comparison method of Sec. 1.1 and Sec. 6): node i
  *       ranks its neighbours by their degree, largest first, ties by CSR
@@ -87,10 +86,54 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <time.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_ARG 1
 #define ORC_ERR_OOM 2
+
+/* ------------------------------------------------------------------------ */
+/* Threads.  Built with OpenMP, the loops over rows of Alg. 1 run on several */
+/* host threads; every row is still computed by one thread with the same     */
+/* operations in the same order, so results do not depend on the thread      */
+/* count (min / max reductions are exact).                                   */
+/* ------------------------------------------------------------------------ */
+void orc_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int32_t orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Wall-clock seconds of the phases of the last orc_algebraic_distance call:
+ * [0] degrees and init, [1] the k sweeps with their rescales, [2] distances. */
+static double g_phase_s[3];
+
+void orc_last_phase_seconds(double out[3])
+{
+    out[0] = g_phase_s[0]; out[1] = g_phase_s[1]; out[2] = g_phase_s[2];
+}
+
+static double now_s(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, from the definition in Salmon, Moraes, Dror, Shaw,        */
@@ -202,11 +245,13 @@ void orc_weighted_degree(int64_t n, const int64_t *rp, const double *w, double *
 static void rescale_vector(int64_t n, const double *D, double *x)
 {
     double lo = INFINITY, hi = -INFINITY;
+#pragma omp parallel for reduction(min:lo) reduction(max:hi) schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         if (!(D[i] > 0.0)) continue;
         if (x[i] < lo) lo = x[i];
         if (x[i] > hi) hi = x[i];
     }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         if (!(D[i] > 0.0)) continue;
         x[i] = (hi > lo) ? (x[i] - lo) / (hi - lo) - 0.5 : 0.0;
@@ -228,19 +273,34 @@ int orc_algebraic_distance(int64_t n, const int64_t *rp, const int32_t *ci, cons
                            const double *x0, double *x_final, double *rho)
 {
     if (n < 0 || R < 1 || k < 0) return ORC_ERR_ARG;
+    const double t0 = now_s();
+    double t_sweeps = 0.0, t_dist = 0.0, t_init = 0.0;
     int64_t m = orc_count_edges(n, rp, ci);
     double *D = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *x = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *y = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *acc = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
-    if (!D || !x || !y || !acc) { free(D); free(x); free(y); free(acc); return ORC_ERR_OOM; }
+    int64_t *e0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));   /* first edge id of row i */
+    if (!D || !x || !y || !acc || !e0) { free(D); free(x); free(y); free(acc); free(e0); return ORC_ERR_OOM; }
     orc_weighted_degree(n, rp, w, D);
+    e0[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t up = 0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) up += ci[p] > i;
+        e0[i + 1] = e0[i] + up;
+    }
+    t_init += now_s() - t0;
 
     for (int64_t e = 0; e < m; ++e) acc[e] = 0.0;                       /* R_ij = 0 */
     for (int32_t r = 0; r < R; ++r) {                                   /* test vectors */
+        double ta = now_s();
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i)                                 /* x <- rand */
             x[i] = x0 ? x0[i * R + r] : orc_test_value(seed, stream, i, r);
+        double tb = now_s();
+        t_init += tb - ta;
         for (int32_t t = 0; t < k; ++t) {                               /* JOR sweeps */
+#pragma omp parallel for schedule(dynamic, 1024)
             for (int64_t i = 0; i < n; ++i) {
                 if (!(D[i] > 0.0)) { y[i] = x[i]; continue; }
                 double s = 0.0;
@@ -252,15 +312,22 @@ int orc_algebraic_distance(int64_t n, const int64_t *rp, const int32_t *ci, cons
             if (rescale_mode == 0) rescale_vector(n, D, x);
         }
         if (rescale_mode == 1) rescale_vector(n, D, x);                 /* rescale back */
+        ta = now_s();
+        t_sweeps += ta - tb;
         if (x_final)
             for (int64_t i = 0; i < n; ++i) x_final[i * R + r] = x[i];
-        int64_t e = 0;                                                  /* R_ij += (x_i-x_j)^2 */
-        for (int64_t i = 0; i < n; ++i)
+#pragma omp parallel for schedule(dynamic, 1024)
+        for (int64_t i = 0; i < n; ++i) {                               /* R_ij += (x_i-x_j)^2 */
+            int64_t e = e0[i];
             for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
                 if (ci[p] > i) { double d = x[i] - x[ci[p]]; acc[e] += d * d; ++e; }
+        }
+        t_dist += now_s() - ta;
     }
-    int64_t e = 0;
-    for (int64_t i = 0; i < n; ++i)
+    const double tc = now_s();
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t e = e0[i];
         for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
             if (ci[p] > i) {
                 double s = sqrt(acc[e]);
@@ -268,7 +335,12 @@ int orc_algebraic_distance(int64_t n, const int64_t *rp, const int32_t *ci, cons
                 rho[e] = s;
                 ++e;
             }
-    free(D); free(x); free(y); free(acc);
+    }
+    t_dist += now_s() - tc;
+    g_phase_s[0] = t_init;
+    g_phase_s[1] = t_sweeps;
+    g_phase_s[2] = t_dist;
+    free(D); free(x); free(y); free(acc); free(e0);
     return ORC_OK;
 }
 
@@ -442,10 +514,9 @@ static int cmp_bin_key(const void *a, const void *b)
 /*
  * Selection rank of every CSR entry under SparsifyB; node i keeps its entries
  * of rank < T(d_i, e).  For row i with distances rho_1..rho_d (CSR order):
- *   mean and sigma (population) by sequential FP32 sums in CSR order;
+ *   mean and sigma (population) by sequential FP64 sums in CSR order;
  *   sigma == 0: one bin; else h = 3.5 sigma / cbrt(d), bin = floor((rho - min) / h),
- *   all in FP32 with each operation rounded on its own (cbrt(d): FP64 cbrt
- *   rounded to FP32);
+ *   all in FP64;
  *   entries of a bin in order of (Philox word of the edge id, position);
  *   bins in order of (Philox word of (i, 1 + bin), bin);
  *   selection order = round robin over the bins: round r takes the r-th entry
@@ -473,27 +544,25 @@ int orc_binned_ranks(int64_t n, const int64_t *rp, const int32_t *ci, const doub
     for (int64_t i = 0; i < n; ++i) {
         const int64_t p0 = rp[i], d = rp[i + 1] - p0;
         if (d == 0) continue;
-        /* FP32 throughout, each operation rounded on its own (reading R13) */
-        float sum = 0.0f, lo = (float)score[eid[p0]], hi = lo;
+        double sum = 0.0, lo = score[eid[p0]], hi = lo;
         for (int64_t t = 0; t < d; ++t) {
-            const float x = (float)score[eid[p0 + t]];
-            sum = sum + x;
+            const double x = score[eid[p0 + t]];
+            sum += x;
             if (x < lo) lo = x;
             if (x > hi) hi = x;
         }
-        const float mean = sum / (float)d;
-        float q = 0.0f;
+        const double mean = sum / (double)d;
+        double q = 0.0;
         for (int64_t t = 0; t < d; ++t) {
-            const float dx = (float)score[eid[p0 + t]] - mean;
-            const float sq = dx * dx;
-            q = q + sq;
+            const double dx = score[eid[p0 + t]] - mean;
+            q += dx * dx;
         }
-        const float sigma = sqrtf(q / (float)d);
-        const float h = 3.5f * sigma / (float)cbrt((double)d);
+        const double sigma = sqrt(q / (double)d);
+        const double h = 3.5 * sigma / cbrt((double)d);
         int64_t nbins = 1;
         for (int64_t t = 0; t < d; ++t) {
             int64_t b = 0;
-            if (sigma > 0.0f && hi > lo) b = (int64_t)floorf(((float)score[eid[p0 + t]] - lo) / h);
+            if (sigma > 0.0 && hi > lo) b = (int64_t)floor((score[eid[p0 + t]] - lo) / h);
             a[t].bin = b;
             a[t].u = bin_word(seed, (uint64_t)eid[p0 + t], 0u);
             a[t].t = t;

@@ -201,3 +201,20 @@ def test_edge_order_and_counts():
 def test_weighted_degree():
     g = random_graph(30, 0.3, 2, True)
     np.testing.assert_allclose(oracle.weighted_degree(g.row_ptr, g.col, wts(g)), dense_W(g).sum(1), rtol=1e-15)
+
+
+def test_thread_count_does_not_change_the_distances():
+    """The oracle's row loops may run on several host threads; each row is still
+    one thread's sequential sum, so the FP64 distances are bit-identical."""
+    g = graphgen.rmat(11, 16, seed=6)
+    w = graphgen.uniform_edge_weights(g.m, seed=2)
+    gw = graphgen.with_edge_weights(g, w)
+    out = []
+    for t in (1, max(2, oracle.max_threads())):
+        oracle.set_threads(t)
+        out.append(oracle.algebraic_distance(gw.row_ptr, gw.col, gw.weight.astype(np.float64), R=8, k=7,
+                                             omega=0.45, seed=3))
+    oracle.set_threads(oracle.max_threads())
+    np.testing.assert_array_equal(out[0], out[1])
+    ph = oracle.last_phase_seconds()
+    assert set(ph) == {"init", "sweeps", "distance"} and all(v >= 0 for v in ph.values())
