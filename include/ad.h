@@ -271,12 +271,13 @@ ad_status ad_select_per_node(ad_graph_t g, const float *score, double e, ad_mode
 
 /*
  * Picks the launch shape of the JOR sweep (Alg. 1) for this graph, R and
- * storage by timing the candidates on the handle: lanes per row (the natural
- * 16-byte-chunk layout, and half as many lanes with two chunks each) x
- * resident CTAs per SM (as many as fit, 5, 4).  Each candidate runs a short
+ * storage by timing the candidates on the handle: resident CTAs per SM of the
+ * streaming sweep (as many as fit, and 2), which also sets how many equal
+ * ranges of CSR entries the sweep is cut into.  Each candidate runs a short
  * distance computation (k = 4) three times; the fastest shape is kept on the
  * handle and used by every later call with this R and storage.  The result
- * depends only on the shape through the order of FP32 additions.
+ * depends on the shape only through the order of FP32 additions (where the
+ * ranges cut rows).
  *   lanes_per_row, chunks_per_lane, ctas_per_sm (0 = as many as fit): the
  *   chosen shape; each may be NULL.
  * Errors: AD_ERR_INVALID_ARG, AD_ERR_OOM, AD_ERR_CUDA.
@@ -307,6 +308,19 @@ ad_status ad_sparsify_binned(ad_graph_t g, const float *score, double fraction, 
                              int64_t *n_kept, double *e_used);
 
 /*
+ * The per-entry quantities behind ad_sparsify_binned (Alg. 3, Sec. 4), for
+ * inspection and testing: rank_out[nnz] receives the SparsifyB selection rank
+ * of every CSR entry inside its row (node i keeps its entries of rank <
+ * T(d_i, e)), bin_out[nnz] (may be NULL) the bin floor((rho - min) / h) of the
+ * entry in its row.  Both are uint32 in CSR order, host or device memory.
+ * score and seed as in ad_sparsify_binned.  The per-row mean and sigma are
+ * FP64 sums over the lanes of a warp, so a bin can differ from one computed
+ * with sequential FP64 sums only when (rho - min) / h lies within a few units
+ * in the last place of an integer.  Errors: as ad_sparsify_binned.
+ */
+ad_status ad_binned_ranks(ad_graph_t g, const float *score, uint64_t seed, uint32_t *rank_out, uint32_t *bin_out);
+
+/*
  * Local Degree, the method the paper compares against (Sec. 1.1, Sec. 6;
  * Lindner et al.): every node takes the edges to its T(d, e) neighbours of
  * largest degree (ties: smaller neighbour position in the row), an edge is
@@ -334,11 +348,14 @@ ad_status ad_sparsify_local_degree(ad_graph_t g, double fraction, uint8_t *keep_
  * (AD_ERR_INVALID_ARG beyond).  The first call on a device looks the array
  * up (cudaGetSymbolAddress) and should come before any stream capture.  All
  * calls on a device share the array: each call rewrites what it reads, and
- * calls that overlap on the GPU race, so the caller must order them.  The
- * call waits for its score check (one small device-to-host copy); the
- * selection itself is queued on stream and complete after the stream is
- * synchronised.  Errors: AD_ERR_INVALID_ARG (size, fraction, mode, host
- * pointers, negative or non-finite scores), AD_ERR_CUDA.
+ * calls that overlap on the GPU race, so the caller must order them.  Every
+ * call checks the scores on the device and then waits on the host for the
+ * result (a device-to-host copy followed by cudaStreamSynchronize(stream)),
+ * so that it can return an error before any selection work is queued; the
+ * selection itself is then queued on stream and is complete after the stream
+ * is synchronised.  *n_kept is written only when the call succeeds.
+ * Errors: AD_ERR_INVALID_ARG (size, fraction, mode, host pointers, negative
+ * or non-finite scores), AD_ERR_CUDA.
  */
 ad_status ad_select_whole_graph_noalloc(const float *score, int64_t m, double fraction, ad_mode mode, uint8_t *keep,
                                         int64_t *n_kept, void *stream);
@@ -393,6 +410,51 @@ ad_status ad_ml_level_size(ad_ml_t ml, int32_t level, int64_t *n, int64_t *m);
  */
 ad_status ad_ml_sparsify(ad_ml_t ml, const double *ratios, int32_t n_ratios, double target_fraction,
                          uint8_t *keep_out, int64_t *n_kept, double *r_used);
+
+/*
+ * MLSparsify(G_f, ratios) of Alg. 6 in one call: builds the hierarchy as
+ * ad_ml_build does, runs the upward half as ad_ml_sparsify does, writes the
+ * kept set of the input graph and releases the hierarchy.  ratios[l]
+ * (l = 0 .. n_ratios - 1, host memory) is the ratio of the l-th coarsest
+ * level in ad_ml_sparsify's convention (-1: not sparsified, otherwise the
+ * fraction of that level's edges to keep, or with target_fraction >= 0 a
+ * marker of the levels that share the fitted ratio); levels past the end of
+ * the vector are not sparsified, so the caller need not know the number of
+ * levels in advance.  ratios may be NULL when n_ratios = 0 (nothing is
+ * sparsified: every edge is kept).  keep_out[m] uint8, host or device;
+ * *n_levels_out (may be NULL) receives the number of levels built.  g must
+ * not be a batch; its kept scores are replaced by the level-0 distances.
+ * Errors: those of ad_ml_build and ad_ml_sparsify.
+ */
+ad_status ad_multilevel(ad_graph_t g, const ad_ml_params *params, const double *ratios, int32_t n_ratios,
+                        double target_fraction, uint8_t *keep_out, int32_t *n_levels_out);
+
+/*
+ * Inspection of level `level` of a hierarchy, for checking Alg. 6 level by
+ * level: the level's graph as ad_graph_export writes it (row_ptr[n_l + 1],
+ * col[nnz_l], weight[nnz_l] FP32 or *has_weight = 0 for unit weights), the
+ * distances of the downward pass rho[m_l] (Alg. 1 with Philox stream 2 level),
+ * and the maps to level + 1: agg[n_l] (coarse vertex of each vertex under
+ * Eq. (P), -1 for degree-0 vertices) and fine_to_coarse[m_l] (coarse edge of
+ * each edge, -1 inside an aggregate).  Every pointer may be NULL; host or
+ * device memory.  Errors: AD_ERR_INVALID_ARG (level), AD_ERR_STATE (agg or
+ * fine_to_coarse asked of the coarsest level).
+ */
+ad_status ad_ml_level_export(ad_ml_t ml, int32_t level, int64_t *row_ptr, int32_t *col, float *weight,
+                             int32_t *has_weight, float *rho, int32_t *agg, int64_t *fine_to_coarse);
+
+/*
+ * Upward trace: with enable != 0, later ad_ml_sparsify calls (and, for a
+ * fitted target fraction, their final pass) record per level the edges left
+ * after the coarser level's removals, the edges kept at the level and the
+ * distances recomputed on the kept subgraph G_f^s of Alg. 6 (NaN where an
+ * edge is not in it or the level is not sparsified); ad_ml_level_trace reads
+ * them (inherited[m_l], kept[m_l] uint8; rho_up[m_l] FP32; each may be NULL;
+ * host or device memory).  Tracing holds 6 bytes per edge of every level.
+ * Errors: AD_ERR_INVALID_ARG, AD_ERR_STATE (no traced call yet).
+ */
+ad_status ad_ml_set_trace(ad_ml_t ml, int32_t enable);
+ad_status ad_ml_level_trace(ad_ml_t ml, int32_t level, uint8_t *inherited, uint8_t *kept, float *rho_up);
 
 /* Ratio vector of the level-span experiments of Sec. 6 for an n_levels
  * hierarchy: segment 1 = coarsest, 2 = middle, 3 = finest levels;

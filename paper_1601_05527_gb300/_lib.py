@@ -72,6 +72,7 @@ _SIGS = {
     "ad_sparsify_scores": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, ctypes.c_int, _VP, _PI64, _PD]),
     "ad_select_per_node": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, _VP, _PI64]),
     "ad_sparsify_binned": (ctypes.c_int, [_VP, _VP, _D, _U64, _VP, _PI64, _PD]),
+    "ad_binned_ranks": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
     "ad_graph_autotune": (ctypes.c_int, [_VP, _I32, ctypes.c_int, _PI32, _PI32, _PI32]),
     "ad_sparsify_local_degree": (ctypes.c_int, [_VP, _D, _VP, _PI64, _PD]),
     "ad_select_whole_graph_noalloc": (ctypes.c_int, [_VP, _I64, _D, ctypes.c_int, _VP, _PI64, _VP]),
@@ -81,6 +82,10 @@ _SIGS = {
     "ad_ml_sparsify": (ctypes.c_int, [_VP, _VP, _I32, _D, _VP, _PI64, _PD]),
     "ad_ml_segment_ratios": (ctypes.c_int, [_I32, _I32, _I32, _D, _VP]),
     "ad_ml_destroy": (ctypes.c_int, [_VP]),
+    "ad_multilevel": (ctypes.c_int, [_VP, ctypes.POINTER(ad_ml_params), _VP, _I32, _D, _VP, _PI32]),
+    "ad_ml_level_export": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _PI32, _VP, _VP, _VP]),
+    "ad_ml_set_trace": (ctypes.c_int, [_VP, _I32]),
+    "ad_ml_level_trace": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP]),
     "ad_coarsen": (ctypes.c_int, [_VP, _VP, _D, _VP, _PI64, ctypes.POINTER(_VP), _VP]),
 }
 
@@ -127,7 +132,8 @@ class _Arr:
             import torch
             if isinstance(x, torch.Tensor):
                 tdt = {np.int64: torch.int64, np.int32: torch.int32, np.float32: torch.float32,
-                       np.uint8: torch.uint8, np.float64: torch.float64}[dtype]
+                       np.uint8: torch.uint8, np.float64: torch.float64,
+                       np.uint32: getattr(torch, "uint32", torch.int32)}[dtype]
                 if x.dtype != tdt:
                     raise TypeError(f"expected {tdt}, got {x.dtype}")
                 if not x.is_contiguous():
@@ -323,6 +329,13 @@ def ad_sparsify_binned(g, score, fraction, seed, keep_out):
     return nk.value, eu.value
 
 
+def ad_binned_ranks(g, score, seed, rank_out, bin_out=None):
+    """Per-entry SparsifyB (Alg. 3) selection rank and bin, uint32 in CSR order;
+    score None = the handle's distances."""
+    s, r, b = _Arr(score, np.float32), _Arr(rank_out, np.uint32), _Arr(bin_out, np.uint32)
+    _check(load().ad_binned_ranks(g, s.ptr, int(seed) & (2**64 - 1), r.ptr, b.ptr))
+
+
 def ad_sparsify_local_degree(g, fraction, keep_out):
     """Local Degree (the paper's comparison method) to a target fraction: (n_kept, e_used)."""
     k = _Arr(keep_out, np.uint8)
@@ -381,6 +394,53 @@ def ad_ml_segment_ratios(n_levels, segment, level_span, value):
 def ad_ml_destroy(ml):
     if ml is not None:
         _check(load().ad_ml_destroy(ml))
+
+
+def ad_ml_level_export(ml, level):
+    """Level `level` of a hierarchy: dict with row_ptr, col, weight (None: unit), rho
+    (downward distances) and, below the coarsest level, agg and f2c."""
+    n, m = ad_ml_level_size(ml, level)
+    L = ad_ml_levels(ml)
+    rp = np.zeros(n + 1, np.int64)
+    nnz = 2 * m
+    ci = np.zeros(max(nnz, 1), np.int32)
+    w = np.zeros(max(nnz, 1), np.float32)
+    hw = ctypes.c_int32()
+    rho = np.zeros(max(m, 1), np.float32)
+    agg = np.zeros(max(n, 1), np.int32) if level < L - 1 else None
+    f2c = np.zeros(max(m, 1), np.int64) if level < L - 1 else None
+    _check(load().ad_ml_level_export(ml, int(level), rp.ctypes.data, ci.ctypes.data, w.ctypes.data, ctypes.byref(hw),
+                                     rho.ctypes.data, None if agg is None else agg.ctypes.data,
+                                     None if f2c is None else f2c.ctypes.data))
+    return {"row_ptr": rp, "col": ci[:nnz], "weight": w[:nnz] if hw.value else None, "rho": rho[:m],
+            "agg": None if agg is None else agg[:n], "f2c": None if f2c is None else f2c[:m]}
+
+
+def ad_ml_set_trace(ml, enable=True):
+    _check(load().ad_ml_set_trace(ml, int(bool(enable))))
+
+
+def ad_ml_level_trace(ml, level):
+    """(inherited, kept, rho_up) of one level from the last traced ad_ml_sparsify call."""
+    _, m = ad_ml_level_size(ml, level)
+    inh = np.zeros(max(m, 1), np.uint8)
+    kp = np.zeros(max(m, 1), np.uint8)
+    ru = np.zeros(max(m, 1), np.float32)
+    _check(load().ad_ml_level_trace(ml, int(level), inh.ctypes.data, kp.ctypes.data, ru.ctypes.data))
+    return inh[:m], kp[:m], ru[:m]
+
+
+def ad_multilevel(g, ratios, target_fraction, keep_out, *, R, k, omega, seed, Q=0.5, coarsest_n=1000, max_levels=64,
+                  mode="local", storage="fp32"):
+    """Alg. 6 in one call; ratios[0] belongs to the coarsest level.  Returns the number of levels."""
+    p = ad_ml_params(int(R), int(k), float(omega), int(seed) & (2**64 - 1), float(Q), int(coarsest_n),
+                     int(max_levels), MODES.get(mode, mode), STORAGES.get(storage, storage))
+    r = None if ratios is None else np.ascontiguousarray(ratios, dtype=np.float64)
+    kk = _Arr(keep_out, np.uint8)
+    nl = ctypes.c_int32()
+    _check(load().ad_multilevel(g, ctypes.byref(p), None if r is None else r.ctypes.data,
+                                0 if r is None else len(r), float(target_fraction), kk.ptr, ctypes.byref(nl)))
+    return nl.value
 
 
 def ad_coarsen(g, score, Q, agg_out, fine_to_coarse_out=None, want_graph=True):

@@ -215,6 +215,15 @@ struct DevBuf {
 constexpr int kChunk = AD_CHUNK;
 constexpr int kBig = AD_CHUNK;
 
+// Plan of the streaming sweep (k_sweep_stream): for S ranges of equal length of
+// the long rows' entries, the first row of each range and the split-row counters.
+struct StreamPlan {
+    int32_t S_req = 0;              // range count asked for
+    int32_t S = 0;                  // ranges used (fewer on small graphs)
+    int32_t *k0 = nullptr;          // [S]
+    uint32_t *counter = nullptr;    // [S], zero between launches
+};
+
 struct RowPlan {
     int small_max = 0;          // degree bound of the small class
     int groups = 0;             // lane groups per warp the plan was built for
@@ -248,6 +257,7 @@ struct ad_graph_s {
     int32_t *col = nullptr;
     float *w = nullptr;          // nullptr = unit weights
     double *D = nullptr;         // weighted degree (FP64)
+    uint8_t *dexact = nullptr;   // [n] weighted graphs: 1 where every partial sum of the row's weights is exact in FP64
     float *Dinv = nullptr;       // 1 / D (0 for isolated vertices)
     int64_t *upos = nullptr;     // first CSR position of row i with col > i
     int64_t *eoff = nullptr;     // edge id of that position; eoff[n] = m
@@ -266,6 +276,12 @@ struct ad_graph_s {
 
     // work plans keyed by lane-group count
     std::vector<ad::RowPlan> sweep_plans, dist_plans;
+    // streaming sweep (built once): long rows with their sequence and CSR begins, short rows
+    // as (row, CSR begin, degree, 0); plans keyed by the requested range count
+    int32_t *lrow = nullptr, *lbeg = nullptr, *lcsr = nullptr, *srows = nullptr;
+    int64_t n_long = 0, n_short = 0, nnz_long = 0;
+    bool have_stream_rows = false;
+    std::vector<ad::StreamPlan> stream_plans;
 
     // scores of the last ad_algebraic_distance call
     float *rho = nullptr;
@@ -356,6 +372,7 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
 ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, const void *x_in, void *x_out,
                      const uint32_t *pmin, const uint32_t *pmax, uint32_t *mn, uint32_t *mx);
 ad_status get_row_plan(ad_graph_t g, int groups, bool upper, RowPlan **out);
+ad_status get_stream_plan(ad_graph_t g, int32_t S, StreamPlan **out);   // sweep.cu
 void natural_shape(int R, ad_storage storage, int *lanes_per_row, int *chunks_per_lane);   // sweep.cu
 
 // selection (select.cu)
@@ -370,7 +387,8 @@ ad_status select_per_node_fit_ranked(ad_graph_t g, const uint32_t *rank_dev, dou
 ad_status select_local_degree(ad_graph_t g, double fraction, uint8_t *keep_dev, int64_t *n_kept, double *e_used);
 
 // SparsifyB order (binned.cu)
-ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev);
+ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev,
+                       uint32_t *bin_dev = nullptr);
 
 ad_status check_scores(ad_graph_t g, const float *score);
 void free_sel_cache(ad_graph_t g);

@@ -439,10 +439,7 @@ extern "C" ad_status ad_graph_autotune(ad_graph_t g, int32_t R, ad_storage stora
     natural_shape(R, storage, &nat_lpr, &nat_cpl);
     struct Cand { int lpr, cpl, per_sm; };
     std::vector<Cand> cands;
-    std::vector<std::pair<int, int>> shapes = {{nat_lpr, nat_cpl}};
-    if (nat_lpr >= 2 && nat_cpl == 1) shapes.push_back({nat_lpr / 2, 2});
-    for (const auto &sh : shapes)
-        for (int per_sm : {0, 5, 4}) cands.push_back({sh.first, sh.second, per_sm});
+    for (int per_sm : {0, 2}) cands.push_back({nat_lpr, nat_cpl, per_sm});
     int best = 0;
     float best_ms = 0.f;
     if (g->m > 0) {
@@ -576,6 +573,34 @@ extern "C" ad_status ad_sparsify_binned(ad_graph_t g, const float *score, double
     if (n_kept) *n_kept = kept;
     if (e_used) *e_used = e;
     return AD_OK;
+}
+
+extern "C" ad_status ad_binned_ranks(ad_graph_t g, const float *score, uint64_t seed, uint32_t *rank_out,
+                                     uint32_t *bin_out) {
+    if (!g) return fail(AD_ERR_INVALID_ARG, "NULL graph");
+    if (!rank_out && g->nnz > 0) return fail(AD_ERR_INVALID_ARG, "rank_out is NULL");
+    if (g->nnz == 0) return AD_OK;
+    DevBuf tmp_s, ranks, bins;
+    const float *sd = g->rho;
+    if (score) {
+        const void *p = nullptr;
+        AD_TRY(stage_in(g, score, g->m * sizeof(float), tmp_s, &p));
+        sd = static_cast<const float *>(p);
+        AD_TRY(check_scores(g, sd));
+    } else if (!g->have_rho) {
+        return fail(AD_ERR_STATE, "no distances: call ad_algebraic_distance first or pass scores");
+    }
+    const size_t bytes = sizeof(uint32_t) * g->nnz;
+    ad_status st = ensure(g, ranks, bytes + 16);
+    if (st == AD_OK && bin_out) st = ensure(g, bins, bytes + 16);
+    if (st == AD_OK)
+        st = binned_ranks(g, sd, seed, static_cast<uint32_t *>(ranks.ptr),
+                          bin_out ? static_cast<uint32_t *>(bins.ptr) : nullptr);
+    if (st == AD_OK) st = copy_out(g, rank_out, ranks.ptr, bytes);
+    if (st == AD_OK && bin_out) st = copy_out(g, bin_out, bins.ptr, bytes);
+    for (DevBuf *b : {&tmp_s, &ranks, &bins})
+        if (b->ptr) dfree(g, b->ptr);
+    return st;
 }
 
 extern "C" ad_status ad_sparsify_local_degree(ad_graph_t g, double fraction, uint8_t *keep_out, int64_t *n_kept,

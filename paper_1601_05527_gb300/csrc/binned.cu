@@ -1,9 +1,9 @@
 // binned.cu -- selection order of SparsifyB (Alg. 3) on sm_103a.
 //
 // Per node i of degree d, with the distances rho of its incident edges:
-//   mean and sigma (population) by sequential FP32 sums in CSR order,
-//   bin width h = 3.5 sigma / cbrt(d) (the rule quoted in Sec. 4), bin of an
-//   entry = floor((rho - min) / h), a single bin when sigma = 0;
+//   mean and sigma (population) in FP64, bin width h = 3.5 sigma / cbrt(d)
+//   (the rule quoted in Sec. 4), bin of an entry = floor((rho - min) / h) in
+//   FP64, a single bin when sigma = 0;
 //   entries of a bin in order of a Philox word of the edge id, bins in order
 //   of a Philox word of (i, 1 + bin); the selection order is a round robin
 //   over the bins -- round r takes the r-th entry of every bin that has one,
@@ -11,17 +11,16 @@
 //   twice.  Node i keeps its entries of rank < T(d, e); the union over the two
 //   ends of an edge and the fit of e are those of Alg. 2 (select.cu).
 //
-// Every floating-point step that decides a bin is an explicitly rounded FP32
-// operation (no contraction), in the same order as the plain definition, and
-// cbrt(d) comes from the host's FP64 cbrt rounded to FP32, so the bins are
-// exactly those of the definition given the same FP32 distances.  (FP32, not
-// FP64: the per-row sums are long dependent chains, and FP64 runs on a narrow
-// pipe on this part.)
+// The row sums are FP64 reductions over the lanes of one warp (the plain
+// definition sums sequentially; the two differ only in the rounding order of
+// the FP64 sums, far below the FP32 resolution of the distances).  Every other
+// step that decides a bin is the same IEEE FP64 operation as in the
+// definition, and cbrt(d) comes from the host's FP64 cbrt.
 //
-// Pipeline: per-row statistics (one thread per row, sequential), per-entry
-// bin and Philox word, a stable radix sort by word and then by (row, bin),
-// runs of equal (row, bin) = the non-empty bins, their order inside the row,
-// and per entry the round-robin rank (a pass over the row's bins).
+// Pipeline: per-row statistics (one warp per row), per-entry bin and Philox
+// word, a stable radix sort by word and then by (row, bin), runs of equal
+// (row, bin) = the non-empty bins, their order inside the row, and per entry
+// the round-robin rank (a pass over the row's bins).
 #include "ad_internal.cuh"
 
 #include <algorithm>
@@ -45,71 +44,63 @@ __global__ void k_bin_gather(const int64_t *eid, const float *score, int64_t nnz
         xs[p] = score[eid[p]];
 }
 
-// per row: lo = min rho, h = bin width (0: a single bin); FP32 with every
-// operation rounded on its own, sums sequential in CSR order, as the
-// definition states them.  The sums are one dependent chain per row, so the
-// loads run a block of 32 ahead of it (kept in registers).
-constexpr int kStatBlock = 32;
-__device__ __forceinline__ void stat_load(const float *x, int64_t base, int64_t d, float (&buf)[kStatBlock]) {
+// per row, one warp: lo = min rho, h = bin width in FP64 (0: a single bin).
+// Each lane sums every 32nd distance of the row; the lane sums are then added
+// by a butterfly.  Every operation is an explicitly rounded FP64 one.
+__device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
-    for (int u = 0; u < kStatBlock; ++u) buf[u] = base + u < d ? x[base + u] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-__global__ void k_bin_stats(const int64_t *rp, const float *xs, const int32_t *dc, const float *cbrt_dc, int64_t n,
-                            float *lo_out, float *h_out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_bin_stats(const int64_t *rp, const float *xs, const int32_t *dc, const double *cbrt_dc, int64_t n,
+                            float *lo_out, double *h_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += W) {
         const int64_t p0 = rp[i], d = rp[i + 1] - p0;
-        if (d == 0) continue;
+        if (d == 0) continue;   // uniform over the warp
         const float *x = xs + p0;
-        float sum = 0.f, lo = x[0], hi = lo;
-        float cur[kStatBlock], nxt[kStatBlock];
-        stat_load(x, 0, d, cur);
-        for (int64_t t0 = 0; t0 < d; t0 += kStatBlock) {
-            if (t0 + kStatBlock < d) stat_load(x, t0 + kStatBlock, d, nxt);
-#pragma unroll
-            for (int u = 0; u < kStatBlock; ++u) {
-                if (t0 + u < d) {
-                    const float v = cur[u];
-                    sum = __fadd_rn(sum, v);
-                    lo = v < lo ? v : lo;
-                    hi = v > hi ? v : hi;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kStatBlock; ++u) cur[u] = nxt[u];
+        double sum = 0.0;
+        float lo = INFINITY, hi = -INFINITY;
+        for (int64_t t = lane; t < d; t += 32) {
+            const float v = x[t];
+            sum = __dadd_rn(sum, (double)v);
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
         }
-        const float mean = __fdiv_rn(sum, (float)d);
-        float q = 0.f;
-        stat_load(x, 0, d, cur);
-        for (int64_t t0 = 0; t0 < d; t0 += kStatBlock) {
-            if (t0 + kStatBlock < d) stat_load(x, t0 + kStatBlock, d, nxt);
+        sum = warp_sum_f64(sum);
 #pragma unroll
-            for (int u = 0; u < kStatBlock; ++u) {
-                if (t0 + u < d) {
-                    const float dx = __fsub_rn(cur[u], mean);
-                    q = __fadd_rn(q, __fmul_rn(dx, dx));
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kStatBlock; ++u) cur[u] = nxt[u];
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         }
-        const float sigma = __fsqrt_rn(__fdiv_rn(q, (float)d));
-        const float h = __fdiv_rn(__fmul_rn(3.5f, sigma), cbrt_dc[dc[i]]);
-        lo_out[i] = lo;
-        h_out[i] = (sigma > 0.f && hi > lo) ? h : 0.f;
+        const double mean = __ddiv_rn(sum, (double)d);
+        double q = 0.0;
+        for (int64_t t = lane; t < d; t += 32) {
+            const double dx = __dsub_rn((double)x[t], mean);
+            q = __dadd_rn(q, __dmul_rn(dx, dx));
+        }
+        q = warp_sum_f64(q);
+        if (lane == 0) {
+            const double sigma = __dsqrt_rn(__ddiv_rn(q, (double)d));
+            const double h = __ddiv_rn(__dmul_rn(3.5, sigma), cbrt_dc[dc[i]]);
+            lo_out[i] = lo;
+            h_out[i] = (sigma > 0.0 && hi > lo) ? h : 0.0;
+        }
     }
 }
 
 // per entry: its bin and Philox word; keys for the first sort (by word), values = positions
 __global__ void k_bin_entries(const int32_t *erow, const int64_t *eid, const float *xs, const float *lo,
-                              const float *h, int64_t nnz, uint64_t seed, uint32_t *bin, uint64_t *keys,
+                              const double *h, int64_t nnz, uint64_t seed, uint32_t *bin, uint64_t *keys,
                               int64_t *vals, unsigned long long *max_bin) {
     unsigned long long mb = 0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = erow[p];
-        const float hi_ = h[i];
+        const double hi_ = h[i];
         int64_t b = 0;
-        if (hi_ > 0.f) b = (int64_t)floorf(__fdiv_rn(__fsub_rn(xs[p], lo[i]), hi_));
+        if (hi_ > 0.0) b = (int64_t)floor(__ddiv_rn(__dsub_rn((double)xs[p], (double)lo[i]), hi_));
         bin[p] = (uint32_t)b;
         mb = (unsigned long long)b > mb ? (unsigned long long)b : mb;
         keys[p] = bin_word(seed, (uint64_t)eid[p], 0u);
@@ -187,17 +178,19 @@ __global__ void k_bin_ranks(const uint64_t *keys, const int64_t *vals, const int
 }
 
 // Selection rank of every CSR entry under SparsifyB, written to rank_dev[nnz]
-// (device).  score_dev: FP32 distances per edge (device).
-ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev) {
+// (device); bin_dev[nnz] (device, may be NULL) receives the bin of every entry.
+// score_dev: FP32 distances per edge (device).
+ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev, uint32_t *bin_dev) {
     const int64_t n = g->n, nnz = g->nnz;
     if (nnz == 0) return AD_OK;
     if (n >= ((int64_t)1 << (64 - kBinBits))) return fail(AD_ERR_INVALID_ARG, "graph too large for binned ranks");
     AD_TRY(ensure_mirror(g));
     AD_TRY(ensure_degree_classes(g));
     // cbrt of every distinct degree, from the host's FP64 cbrt
-    std::vector<float> cb(std::max<int32_t>(g->n_deg_classes, 1));
-    for (int32_t q = 0; q < g->n_deg_classes; ++q) cb[q] = (float)std::cbrt((double)g->distinct_degrees[q]);
-    float *cbrt_dc = nullptr, *lo = nullptr, *h = nullptr, *xs = nullptr;
+    std::vector<double> cb(std::max<int32_t>(g->n_deg_classes, 1));
+    for (int32_t q = 0; q < g->n_deg_classes; ++q) cb[q] = std::cbrt((double)g->distinct_degrees[q]);
+    double *cbrt_dc = nullptr, *h = nullptr;
+    float *lo = nullptr, *xs = nullptr;
     uint32_t *bin = nullptr, *run_word = nullptr;
     uint64_t *keys = nullptr;
     int64_t *vals = nullptr, *flag = nullptr, *run_of = nullptr, *run_start = nullptr, *row_runs = nullptr;
@@ -210,16 +203,17 @@ ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint
     AD_TRY(dalloc_t(g, nnz, &keys));
     AD_TRY(dalloc_t(g, nnz, &vals));
     AD_TRY(dalloc_t(g, 1, &max_bin));
-    AD_TRY(copy_in(g, cbrt_dc, cb.data(), cb.size() * sizeof(float)));
+    AD_TRY(copy_in(g, cbrt_dc, cb.data(), cb.size() * sizeof(double)));
     AD_CUDA_TRY(cudaMemsetAsync(max_bin, 0, sizeof(unsigned long long), g->stream));
     const int big = g->num_sms * 16;
     AD_LAUNCH(k_bin_gather, big, 256, 0, g->stream, g->eid, score_dev, nnz, xs);
-    AD_LAUNCH(k_bin_stats, (int)std::min<int64_t>((n + 127) / 128, big), 128, 0, g->stream, g->rp, xs, g->deg_class,
+    AD_LAUNCH(k_bin_stats, (int)std::min<int64_t>((n + 7) / 8, big), 256, 0, g->stream, g->rp, xs, g->deg_class,
               cbrt_dc, n, lo, h);
     AD_LAUNCH(k_bin_entries, big, 256, 0, g->stream, g->erow, g->eid, xs, lo, h, nnz, seed, bin, keys, vals, max_bin);
     unsigned long long mb = 0;
     AD_TRY(copy_out(g, &mb, max_bin, sizeof(mb)));
     if (mb >= (1ull << kBinBits)) return fail(AD_ERR_INVALID_ARG, "too many bins in one row");
+    if (bin_dev) AD_CUDA_TRY(cudaMemcpyAsync(bin_dev, bin, nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, g->stream));
     AD_TRY(radix_sort_pairs(g, keys, vals, nnz, {0, 8, 16, 24}));            // by Philox word, then position
     AD_LAUNCH(k_bin_rowkeys, big, 256, 0, g->stream, vals, g->erow, bin, nnz, keys);
     std::vector<int> shifts;                                                  // bin bits in use, then row bits

@@ -227,27 +227,59 @@ __global__ void k_degrees(const int64_t *rp, const int32_t *col, const float *w,
 }
 
 // weighted degrees D_i = sum_j w_ij in FP64: a warp per row, lanes strided over
-// the row in a fixed order
-__global__ void k_wdegrees(const int64_t *rp, const float *w, int64_t n, double *D, float *Dinv) {
+// the row.  When the row's weights span few enough binary orders of magnitude,
+// every partial sum of them is an exact FP64 number -- the weights are
+// multiples of the smallest weight's unit in the last place, and d of them stay
+// below 2^(largest exponent + 1 + ceil log2 d) -- so any summation order gives
+// the same bits as summing one after the other in CSR order.  Rows where that
+// bound does not hold are summed one entry after the other in CSR order by one
+// lane.  exact_out[i] records which case row i is (the seed rule relies on it).
+__device__ __forceinline__ int fp32_biased_exponent(float v) { return (int)((__float_as_uint(v) >> 23) & 0xffu); }
+
+__global__ void k_wdegrees(const int64_t *rp, const float *w, int64_t n, double *D, float *Dinv, uint8_t *exact_out) {
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W) {
         const int64_t b = rp[i], e = rp[i + 1];
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four independent loads in flight per lane
+        int emax = 0, emin = 255;
         int64_t p = b + lane;
         for (; p + 96 < e; p += 128) {
-            s0 += (double)w[p];
-            s1 += (double)w[p + 32];
-            s2 += (double)w[p + 64];
-            s3 += (double)w[p + 96];
+            const float w0 = w[p], w1 = w[p + 32], w2 = w[p + 64], w3 = w[p + 96];
+            s0 += (double)w0;
+            s1 += (double)w1;
+            s2 += (double)w2;
+            s3 += (double)w3;
+            emax = max(emax, max(max(fp32_biased_exponent(w0), fp32_biased_exponent(w1)),
+                                 max(fp32_biased_exponent(w2), fp32_biased_exponent(w3))));
+            emin = min(emin, min(min(fp32_biased_exponent(w0), fp32_biased_exponent(w1)),
+                                 min(fp32_biased_exponent(w2), fp32_biased_exponent(w3))));
         }
-        for (; p < e; p += 32) s0 += (double)w[p];
+        for (; p < e; p += 32) {
+            const float w0 = w[p];
+            s0 += (double)w0;
+            emax = max(emax, fp32_biased_exponent(w0));
+            emin = min(emin, fp32_biased_exponent(w0));
+        }
         double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+            emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+        }
+        int lg = 0;
+        while (((int64_t)1 << lg) < e - b) ++lg;   // ceil(log2 d)
+        // bits spanned by every partial sum: (emax - 127 + 1 + lg) - (max(emin, 1) - 150)
+        const bool exact = e == b || emax - max(emin, 1) + lg + 24 <= 53;
         if (lane == 0) {
+            if (!exact) {   // the plain definition's order, one entry after the other
+                s = 0.0;
+                for (int64_t q = b; q < e; ++q) s += (double)w[q];
+            }
             D[i] = s;
             Dinv[i] = s > 0.0 ? (float)(1.0 / s) : 0.f;
+            exact_out[i] = exact ? 1 : 0;
         }
     }
 }
@@ -340,7 +372,8 @@ ad_status recompute_degrees(ad_graph_t g) {
               ucount);
     if (g->w) {
         const int64_t wblocks = std::min<int64_t>((g->n + 7) / 8 + 1, (int64_t)g->num_sms * 64);
-        AD_LAUNCH(k_wdegrees, (int)wblocks, 256, 0, g->stream, g->rp, g->w, g->n, g->D, g->Dinv);
+        if (!g->dexact) AD_TRY(dalloc_t(g, g->n + 1, &g->dexact));
+        AD_LAUNCH(k_wdegrees, (int)wblocks, 256, 0, g->stream, g->rp, g->w, g->n, g->D, g->Dinv, g->dexact);
     }
     int64_t m = 0;
     ad_status st = exclusive_scan_i64(g, ucount, g->eoff, g->n, &m);

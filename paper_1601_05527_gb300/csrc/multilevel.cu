@@ -27,8 +27,14 @@ struct ad_ml_s {
         float *rho = nullptr;       // [m] distances computed on the way down
         int32_t *agg = nullptr;     // [n] aggregate in the next coarser level
         int64_t *f2c = nullptr;     // [m] coarse edge of each edge (-1 inside an aggregate)
+        // upward trace of the last ad_ml_sparsify call (when tracing is on)
+        uint8_t *t_inh = nullptr;   // [m] edges left after the coarser level's removals
+        uint8_t *t_keep = nullptr;  // [m] edges kept at this level
+        float *t_rho = nullptr;     // [m] distances recomputed on the kept subgraph (NaN: not in it / not recomputed)
     };
     std::vector<Level> lv;
+    bool trace = false;
+    bool have_trace = false;
 };
 
 namespace ad {
@@ -43,15 +49,22 @@ __global__ void k_seed_init(const double *D, int64_t n, int8_t *state) {
         state[i] = D[i] > 0.0 ? S_UNDECIDED : S_INACTIVE;
 }
 
-__global__ void k_seed_round(const int64_t *rp, const int32_t *col, const float *w, const double *D, int64_t n,
-                             double Q, int8_t *state, unsigned long long *undecided) {
+// The sums below are exact in any order on rows whose weights pass the
+// exactness bound of the weighted degrees (dexact; unit weights always do), so
+// they equal the sequential sums of the definition bit for bit.  On the other
+// rows a vertex waits until every predecessor is decided and then sums its
+// seed neighbours one after the other in CSR order, as the definition does.
+__global__ void k_seed_round(const int64_t *rp, const int32_t *col, const float *w, const double *D,
+                             const uint8_t *dexact, int64_t n, double Q, int8_t *state, unsigned long long *undecided) {
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     volatile int8_t *vs = state;
     for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W) {
         if (vs[i] != S_UNDECIDED) continue;
         const double Di = D[i];
+        const bool exact = !w || dexact[i];
         double seed_w = 0.0, und_w = 0.0;
+        bool und_any = false;
         for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
             const int32_t j = col[p];
             const double Dj = D[j];
@@ -59,7 +72,7 @@ __global__ void k_seed_round(const int64_t *rp, const int32_t *col, const float 
                 const int8_t sj = vs[j];
                 const double wj = w ? (double)w[p] : 1.0;
                 if (sj == S_SEED) seed_w += wj;
-                else if (sj == S_UNDECIDED) und_w += wj;
+                else if (sj == S_UNDECIDED) { und_w += wj; und_any = true; }
             }
         }
 #pragma unroll
@@ -67,11 +80,24 @@ __global__ void k_seed_round(const int64_t *rp, const int32_t *col, const float 
             seed_w += __shfl_xor_sync(0xffffffffu, seed_w, o);
             und_w += __shfl_xor_sync(0xffffffffu, und_w, o);
         }
+        und_any = __any_sync(0xffffffffu, und_any);
         if (lane == 0) {
             const double lim = Q * Di;
-            if (seed_w > lim) vs[i] = S_F;
-            else if (seed_w + und_w <= lim) vs[i] = S_SEED;
-            else atomicAdd(undecided, 1ull);
+            if (exact) {
+                if (seed_w > lim) vs[i] = S_F;
+                else if (seed_w + und_w <= lim) vs[i] = S_SEED;
+                else atomicAdd(undecided, 1ull);
+            } else if (und_any) {
+                atomicAdd(undecided, 1ull);
+            } else {
+                double s = 0.0;   // successors may already be decided: only predecessors count
+                for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                    const int32_t j = col[p];
+                    const double Dj = D[j];
+                    if ((Dj > Di || (Dj == Di && j < i)) && vs[j] == S_SEED) s += (double)w[p];
+                }
+                vs[i] = s <= lim ? S_SEED : S_F;
+            }
         }
     }
 }
@@ -90,7 +116,8 @@ static ad_status create_seeds(ad_graph_t g, double Q, int8_t *state) {
             return fail(AD_ERR_STATE, "seed selection did not converge");
         }
         AD_CUDA_TRY(cudaMemsetAsync(und, 0, sizeof(unsigned long long), g->stream));
-        AD_LAUNCH(k_seed_round, (int)wblocks, 256, 0, g->stream, g->rp, g->col, g->w, g->D, n, Q, state, und);
+        AD_LAUNCH(k_seed_round, (int)wblocks, 256, 0, g->stream, g->rp, g->col, g->w, g->D, g->dexact, n, Q, state,
+                  und);
         unsigned long long u = 0;
         AD_TRY(copy_out(g, &u, und, sizeof(u)));
         if (u == 0) break;
@@ -422,6 +449,27 @@ __global__ void k_scatter_keep(const int64_t *s2f, const uint8_t *ks, int64_t ms
     if (q < ms) keep[s2f[q]] = ks[q];
 }
 
+__global__ void k_scatter_f32(const int64_t *s2f, const float *src, int64_t ms, float *dst) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < ms) dst[s2f[q]] = src[q];
+}
+
+__global__ void k_fill_nan(float *x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = __int_as_float(0x7fc00000);
+}
+
+// trace buffers of one level (allocated on first use, owned by the level's graph)
+static ad_status trace_buffers(ad_ml_s::Level &v) {
+    ad_graph_t g = v.g;
+    if (!v.t_inh) AD_TRY(dalloc_t(g, g->m + 1, &v.t_inh));
+    if (!v.t_keep) AD_TRY(dalloc_t(g, g->m + 1, &v.t_keep));
+    if (!v.t_rho) AD_TRY(dalloc_t(g, g->m + 1, &v.t_rho));
+    if (g->m > 0) AD_LAUNCH(k_fill_nan, std::max<int>(1, (int)std::min<int64_t>((g->m + 255) / 256, 4096)), 256, 0,
+                            g->stream, v.t_rho, g->m);
+    return AD_OK;
+}
+
 __global__ void k_count_u8(const uint8_t *f, int64_t n, unsigned long long *c) {
     unsigned long long s = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -479,10 +527,14 @@ static ad_status ml_upward(ad_ml_t ml, const std::vector<double> &r, uint8_t *ke
     ad_graph_t owner_c = nullptr;
     for (int l = L - 1; l >= 0; --l) {
         ad_graph_t g = ml->lv[l].g;
+        ad_ml_s::Level &tv = ml->lv[l];
         uint8_t *keep = l == 0 ? keep0 : nullptr;
         if (!keep) AD_TRY(dalloc_t(g, g->m + 1, &keep));
+        if (ml->trace) AD_TRY(trace_buffers(tv));
         if (l == L - 1) {
             AD_CUDA_TRY(cudaMemsetAsync(keep, 1, g->m > 0 ? g->m : 1, g->stream));
+            if (ml->trace && g->m > 0)
+                AD_CUDA_TRY(cudaMemcpyAsync(tv.t_inh, keep, g->m, cudaMemcpyDeviceToDevice, g->stream));
             if (r[l] >= 0.0 && g->m > 0) {
                 int64_t k = 0;
                 double e = 0;
@@ -490,6 +542,8 @@ static ad_status ml_upward(ad_ml_t ml, const std::vector<double> &r, uint8_t *ke
             }
         } else {
             if (g->m > 0) AD_LAUNCH(k_uncoarsen, nblk(g->m), 256, 0, g->stream, ml->lv[l].f2c, keep_c, g->m, keep);
+            if (ml->trace && g->m > 0)
+                AD_CUDA_TRY(cudaMemcpyAsync(tv.t_inh, keep, g->m, cudaMemcpyDeviceToDevice, g->stream));
             if (r[l] >= 0.0 && g->m > 0) {
                 // ComputeAlgDist(G_f^s), then Sparsify(G_f^s)
                 ad_graph_t sub = nullptr;
@@ -510,6 +564,7 @@ static ad_status ml_upward(ad_ml_t ml, const std::vector<double> &r, uint8_t *ke
                         AD_CUDA_TRY(cudaMemsetAsync(keep, 0, g->m, g->stream));
                         AD_CUDA_TRY(cudaStreamSynchronize(sub->stream));
                         AD_LAUNCH(k_scatter_keep, nblk(ms), 256, 0, g->stream, s2f, ks, ms, keep);
+                        if (ml->trace) AD_LAUNCH(k_scatter_f32, nblk(ms), 256, 0, g->stream, s2f, sub->rho, ms, tv.t_rho);
                         AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
                     }
                 }
@@ -518,10 +573,13 @@ static ad_status ml_upward(ad_ml_t ml, const std::vector<double> &r, uint8_t *ke
                 AD_TRY(st);
             }
         }
+        if (ml->trace && g->m > 0)
+            AD_CUDA_TRY(cudaMemcpyAsync(tv.t_keep, keep, g->m, cudaMemcpyDeviceToDevice, g->stream));
         if (keep_c) dfree(owner_c, keep_c);
         keep_c = l == 0 ? nullptr : keep;
         owner_c = g;
     }
+    ml->have_trace = ml->trace;
     return count_kept(ml->lv[0].g, keep0, ml->lv[0].g->m, kept);
 }
 
@@ -533,6 +591,8 @@ static void ml_free(ad_ml_t ml) {
         } else if (v.g) {
             if (v.agg) dfree(v.g, v.agg);
             if (v.f2c) dfree(v.g, v.f2c);
+            for (void *b : {(void *)v.t_inh, (void *)v.t_keep, (void *)v.t_rho})
+                if (b) dfree(v.g, b);
             // level 0's rho is the handle's own score buffer and stays with it
         }
     }
@@ -609,6 +669,41 @@ extern "C" ad_status ad_ml_level_size(ad_ml_t ml, int32_t level, int64_t *n, int
     return AD_OK;
 }
 
+// Inspection of one level (see include/ad.h): its graph, the distances of the
+// downward pass, and the maps to the next coarser level.
+extern "C" ad_status ad_ml_level_export(ad_ml_t ml, int32_t level, int64_t *row_ptr, int32_t *col, float *weight,
+                                        int32_t *has_weight, float *rho, int32_t *agg, int64_t *fine_to_coarse) {
+    if (!ml) return fail(AD_ERR_INVALID_ARG, "NULL hierarchy");
+    if (level < 0 || level >= (int32_t)ml->lv.size()) return fail(AD_ERR_INVALID_ARG, "level out of range");
+    const ad_ml_s::Level &v = ml->lv[level];
+    ad_graph_t g = v.g;
+    if ((agg || fine_to_coarse) && !v.agg) return fail(AD_ERR_STATE, "the coarsest level has no coarser level");
+    AD_TRY(ad_graph_export(g, row_ptr, col, weight, has_weight));
+    if (rho && g->m > 0) AD_TRY(copy_out(g, rho, v.rho, g->m * sizeof(float)));
+    if (agg && g->n > 0) AD_TRY(copy_out(g, agg, v.agg, g->n * sizeof(int32_t)));
+    if (fine_to_coarse && g->m > 0) AD_TRY(copy_out(g, fine_to_coarse, v.f2c, g->m * sizeof(int64_t)));
+    return AD_OK;
+}
+
+extern "C" ad_status ad_ml_set_trace(ad_ml_t ml, int32_t enable) {
+    if (!ml) return fail(AD_ERR_INVALID_ARG, "NULL hierarchy");
+    ml->trace = enable != 0;
+    return AD_OK;
+}
+
+extern "C" ad_status ad_ml_level_trace(ad_ml_t ml, int32_t level, uint8_t *inherited, uint8_t *kept, float *rho_up) {
+    if (!ml) return fail(AD_ERR_INVALID_ARG, "NULL hierarchy");
+    if (level < 0 || level >= (int32_t)ml->lv.size()) return fail(AD_ERR_INVALID_ARG, "level out of range");
+    if (!ml->have_trace) return fail(AD_ERR_STATE, "no traced ad_ml_sparsify call");
+    const ad_ml_s::Level &v = ml->lv[level];
+    ad_graph_t g = v.g;
+    if (g->m == 0) return AD_OK;
+    if (inherited) AD_TRY(copy_out(g, inherited, v.t_inh, g->m));
+    if (kept) AD_TRY(copy_out(g, kept, v.t_keep, g->m));
+    if (rho_up) AD_TRY(copy_out(g, rho_up, v.t_rho, g->m * sizeof(float)));
+    return AD_OK;
+}
+
 extern "C" ad_status ad_ml_sparsify(ad_ml_t ml, const double *ratios, int32_t n_ratios, double target_fraction,
                                     uint8_t *keep_out, int64_t *n_kept, double *r_used) {
     if (!ml || !ratios) return fail(AD_ERR_INVALID_ARG, "NULL argument");
@@ -652,6 +747,30 @@ extern "C" ad_status ad_ml_sparsify(ad_ml_t ml, const double *ratios, int32_t n_
     if (n_kept) *n_kept = kept;
     if (r_used) *r_used = used;
     return AD_OK;
+}
+
+// MLSparsify(G_f, ratios) of Alg. 6 in one call: the downward half
+// (ad_ml_build), the upward half with the ratio vector (ad_ml_sparsify) and
+// the release of the hierarchy.  ratios[l] belongs to the l-th coarsest level;
+// levels past the end of the vector are not sparsified.
+extern "C" ad_status ad_multilevel(ad_graph_t g, const ad_ml_params *params, const double *ratios, int32_t n_ratios,
+                                   double target_fraction, uint8_t *keep_out, int32_t *n_levels_out) {
+    if (!g || !params) return fail(AD_ERR_INVALID_ARG, "NULL argument");
+    if (n_ratios < 0 || (n_ratios > 0 && !ratios)) return fail(AD_ERR_INVALID_ARG, "bad ratio vector");
+    for (int32_t t = 0; t < n_ratios; ++t)
+        if (std::isnan(ratios[t]) || ratios[t] > 1.0) return fail(AD_ERR_INVALID_ARG, "ratios must be <= 1");
+    if (std::isnan(target_fraction) || target_fraction > 1.0)
+        return fail(AD_ERR_INVALID_ARG, "target_fraction must be <= 1");
+    if (!keep_out && g->m > 0) return fail(AD_ERR_INVALID_ARG, "keep_out is NULL");
+    ad_ml_t ml = nullptr;
+    AD_TRY(ad_ml_build(g, params, &ml));
+    const int32_t L = (int32_t)ml->lv.size();
+    std::vector<double> r(L, -1.0);
+    for (int32_t l = 0; l < L && l < n_ratios; ++l) r[l] = ratios[l];
+    const ad_status st = ad_ml_sparsify(ml, r.data(), L, target_fraction, keep_out, nullptr, nullptr);
+    ad_ml_destroy(ml);
+    if (st == AD_OK && n_levels_out) *n_levels_out = L;
+    return st;
 }
 
 extern "C" ad_status ad_ml_segment_ratios(int32_t n_levels, int32_t segment, int32_t level_span, double value,

@@ -1403,9 +1403,11 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocS
 
 static std::mutex g_noalloc_mu;
 static NoAllocScratch *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+static int g_noalloc_sms[kNoAllocMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once per device).
-static ad_status noalloc_scratch(NoAllocScratch **out) {
+// Device address of the scratch array on the current device and its SM count
+// (looked up once per device).
+static ad_status noalloc_scratch(NoAllocScratch **out, int *num_sms) {
     int dev = 0;
     AD_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(AD_ERR_INVALID_ARG, "device id out of range");
@@ -1415,9 +1417,13 @@ static ad_status noalloc_scratch(NoAllocScratch **out) {
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return fail(AD_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        int sms = 0;
+        AD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        g_noalloc_sms[dev] = sms > 0 ? sms : kNumSMs;
         g_noalloc_ptr[dev] = static_cast<NoAllocScratch *>(p);
     }
     *out = g_noalloc_ptr[dev];
+    *num_sms = g_noalloc_sms[dev];
     return AD_OK;
 }
 
@@ -1487,19 +1493,23 @@ extern "C" ad_status ad_select_whole_graph_noalloc(const float *score, int64_t m
     if (m > 0 && (!is_device_ptr(score) || !is_device_ptr(keep)))
         return fail(AD_ERR_INVALID_ARG, "score and keep must be device arrays (nothing is staged)");
     NoAllocScratch *s = nullptr;
-    AD_TRY(noalloc_scratch(&s));
+    int num_sms = kNumSMs;
+    AD_TRY(noalloc_scratch(&s, &num_sms));
     const int64_t K = target_count(m, fraction);
-    if (n_kept) *n_kept = K;
-    if (m == 0) return AD_OK;
+    if (m == 0) {
+        if (n_kept) *n_kept = K;
+        return AD_OK;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int desc = mode == AD_MODE_GLOBAL ? 1 : 0;
     const int64_t ntiles = (m + kTile - 1) / kTile;
     AD_LAUNCH(k_noalloc_init, 64, 256, 0, st, s, m, K, ntiles);
-    AD_LAUNCH(k_check_scores, 152 * 8, 256, 0, st, score, m, &s->bad);
+    AD_LAUNCH(k_check_scores, num_sms * 8, 256, 0, st, score, m, &s->bad);
     unsigned long long bad = 0;
     AD_CUDA_TRY(cudaMemcpyAsync(&bad, &s->bad, sizeof(bad), cudaMemcpyDeviceToHost, st));
     AD_CUDA_TRY(cudaStreamSynchronize(st));
     if (bad != ~0ull) return fail(AD_ERR_INVALID_ARG, "score " + std::to_string(bad) + " is negative or not finite");
+    if (n_kept) *n_kept = K;
     const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
     const uint32_t hi_masks[3] = {0u, 0xFFE00000u, 0xFFFFFC00u};
     for (int pass = 0; pass < 3; ++pass) {

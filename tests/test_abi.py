@@ -85,3 +85,16 @@ def test_entry_points_fail_loudly_without_the_library():
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     lines = r.stdout.strip().splitlines()
     assert len(lines) == 3 and all(l.startswith("raised:") and "missing" in l for l in lines), r.stdout + r.stderr
+
+
+def test_noalloc_entry_point_names_no_allocation():
+    """ad_select_whole_graph_noalloc (for callers that cannot let a library
+    allocate device memory) calls no allocating routine: its body and the
+    helpers it calls in select.cu name no malloc/free or the library's own
+    allocation helpers."""
+    src = open(os.path.join(ROOT, "paper_1601_05527_gb300", "csrc", "select.cu")).read()
+    start = src.index("// Whole-graph selection that allocates nothing")
+    body = re.sub(r"//[^\n]*", "", src[start:])
+    for word in ("cudaMalloc", "cudaFree", "malloc(", "free(", "dalloc", "dfree", "ensure(", "DevBuf",
+                 "stage_in", "copy_in", "copy_out", "new ", "cudaMemPool"):
+        assert word not in body, word

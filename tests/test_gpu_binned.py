@@ -1,14 +1,19 @@
 """GPU parity of SparsifyB (Alg. 3, the binned "mixture" selection of Sec. 4).
 
-Given identical FP32 scores the bins, the random orders and the fitted
-exponent are integer decisions taken with the same FP64 operations on both
-sides, so the kept edge set, its size and e must equal the oracle's exactly."""
+The oracle computes each node's mean, sigma, bin width and bins with
+sequential FP64 sums in CSR order; the GPU sums the same FP64 values over the
+lanes of a warp.  Bins are therefore compared entry by entry with the
+oracle's: a bin may differ only where (rho - min) / h lies within rounding of
+an integer, and the share of such rows is bounded.  On every row whose bins
+agree, the selection ranks (Philox order inside and across bins, round robin)
+must equal the oracle's exactly; where no bin differs, the kept edge set, its
+size and the fitted e must be the oracle's exactly."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_1601_05527_gb300 import graphgen
-from gpu_util import lib
+from gpu_util import jaccard, lib
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +47,34 @@ def scores_for(g, kind, seed):
     return graphgen.random_scores(g.m, 7, seed=seed)   # few distinct values: equal distances, sigma 0 rows
 
 
+def check_bins_and_ranks(L, h, g, s, seed, max_flip_row_share=1e-4):
+    """Bins entry by entry against the oracle, ranks exactly on the rows whose
+    bins agree; returns (entries with a different bin, rows with one)."""
+    rank = np.zeros(g.nnz, np.uint32)
+    bins = np.zeros(g.nnz, np.uint32)
+    L.ad_binned_ranks(h, s, seed, rank, bins)
+    ref_rank, ref_bins = oracle.binned_ranks(g.row_ptr, g.col, s.astype(np.float64), seed, return_bins=True)
+    flip = bins.astype(np.int64) != ref_bins
+    rows = np.repeat(np.arange(g.n), g.degrees())
+    bad_rows = np.unique(rows[flip])
+    agree = ~np.isin(rows, bad_rows)
+    np.testing.assert_array_equal(rank[agree].astype(np.int64), ref_rank[agree])
+    n_rows = int((g.degrees() > 0).sum())
+    assert len(bad_rows) <= max_flip_row_share * max(n_rows, 1), (len(bad_rows), n_rows)
+    return int(flip.sum()), len(bad_rows)
+
+
+def check_keep(L, h, g, s, f, seed, flips):
+    keep = np.zeros(g.m, np.uint8)
+    kept, e = L.ad_sparsify_binned(h, s, f, seed, keep)
+    ref, rk, re_ = oracle.sparsify_binned(g.row_ptr, g.col, s.astype(np.float64), seed, f)
+    if flips == 0:
+        assert kept == rk and e == re_, (f, kept, rk, e, re_)
+        np.testing.assert_array_equal(keep, ref)
+    else:
+        assert jaccard(keep, ref) >= 0.999
+
+
 @pytest.mark.parametrize("name", list(GRAPHS))
 @pytest.mark.parametrize("kind", ["uniform", "skewed", "ties"])
 def test_binned_matches_oracle(name, kind):
@@ -51,11 +84,8 @@ def test_binned_matches_oracle(name, kind):
     h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
     try:
         for f, seed in ((0.0, 1), (0.3, 2), (0.6, 0x1601055270000000), (1.0, 3)):
-            keep = np.zeros(g.m, np.uint8)
-            kept, e = L.ad_sparsify_binned(h, s, f, seed, keep)
-            ref, rk, re_ = oracle.sparsify_binned(g.row_ptr, g.col, s.astype(np.float64), seed, f)
-            assert kept == rk and e == re_, (f, kept, rk, e, re_)
-            np.testing.assert_array_equal(keep, ref)
+            flips, _ = check_bins_and_ranks(L, h, g, s, seed)
+            check_keep(L, h, g, s, f, seed, flips)
     finally:
         L.ad_graph_destroy(h)
 
@@ -90,15 +120,16 @@ def test_binned_rejects_bad_input():
     L.ad_graph_destroy(h)
 
 
-def test_full_size_rmat20_binned_bit_exact():
-    """The benchmark's graph (R-MAT scale 20, 15.7M edges) at 30%."""
+def test_full_size_rmat20_binned():
+    """The benchmark's graph (R-MAT scale 20, 15.7M edges) at 30%: bins against
+    the FP64 oracle entry by entry, exact ranks where they agree, and the kept set."""
     L = lib()
     g = graphgen.rmat(20, 16, seed=2)
     s = (np.random.default_rng(4).random(g.m) ** 2).astype(np.float32)
     h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
-    keep = np.zeros(g.m, np.uint8)
-    kept, e = L.ad_sparsify_binned(h, s, 0.3, 9, keep)
-    L.ad_graph_destroy(h)
-    ref, rk, re_ = oracle.sparsify_binned(g.row_ptr, g.col, s.astype(np.float64), 9, 0.3)
-    assert kept == rk and e == re_
-    np.testing.assert_array_equal(keep, ref)
+    try:
+        flips, rows = check_bins_and_ranks(L, h, g, s, 9, max_flip_row_share=1e-5)
+        print(f"bin flips against the FP64 oracle: {flips} entries in {rows} rows of {int((g.degrees() > 0).sum())}")
+        check_keep(L, h, g, s, 0.3, 9, flips)
+    finally:
+        L.ad_graph_destroy(h)

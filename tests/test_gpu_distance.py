@@ -234,7 +234,7 @@ def test_autotuned_shape_keeps_the_distances(storage, R):
     before = np.zeros(g.m, np.float32)
     L.ad_algebraic_distance(h, R, 12, 0.5, 3, 0, storage, 0, before)
     lpr, cpl, per_sm = L.ad_graph_autotune(h, R, storage)
-    assert lpr >= 1 and cpl in (1, 2) and per_sm in (0, 4, 5)
+    assert lpr >= 1 and cpl in (1, 2) and per_sm in (0, 2)
     after = np.zeros(g.m, np.float32)
     L.ad_algebraic_distance(h, R, 12, 0.5, 3, 0, storage, 0, after)
     L.ad_graph_destroy(h)

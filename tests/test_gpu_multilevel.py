@@ -79,6 +79,31 @@ def test_hierarchy_and_sparsification_against_oracle():
     L.ad_graph_destroy(h)
 
 
+def test_one_shot_multilevel_call_against_oracle():
+    """ad_multilevel (Alg. 6 MLSparsify in one call) on the 20K hierarchy whose
+    levels equal the oracle's: coarse-level control to 40%, and a ratio vector
+    shorter than the hierarchy (the finer levels are then not sparsified)."""
+    L = lib()
+    g = weighted(graphgen.barabasi_albert(20000, 8, seed=11), 12)
+    w64 = g.weight.astype(np.float64)
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, g.weight)
+    ref = oracle.Multilevel(g.row_ptr, g.col, w64, R=16, k=20, omega=0.5, seed=5, Q=0.5, coarsest_n=300, mode="local")
+    Lv = ref.levels
+    keep = np.zeros(g.m, np.uint8)
+    span = max(1, Lv // 3)
+    ratios = oracle.segment_ratios(Lv, "coarse", span, 1.0)
+    nl = L.ad_multilevel(h, ratios[:span], 0.4, keep, R=16, k=20, omega=0.5, seed=5, Q=0.5, coarsest_n=300,
+                         mode="local")
+    assert nl == Lv
+    rkeep, rkept, _ = ref.sparsify(ratios, 0.4)
+    assert keep.sum() >= oracle.target_count(g.m, 0.4)
+    assert jaccard(keep, rkeep) >= 0.99
+    nl = L.ad_multilevel(h, None, -1.0, keep, R=16, k=20, omega=0.5, seed=5, Q=0.5, coarsest_n=300)
+    assert nl == Lv and keep.all()
+    ref.close()
+    L.ad_graph_destroy(h)
+
+
 def test_multilevel_rejects_bad_parameters():
     L = lib()
     g = graphgen.grid2d(10, 10)

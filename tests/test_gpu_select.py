@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_1601_05527_gb300 import graphgen
-from gpu_util import assert_rho_close, entry_weights_f64, jaccard, lib
+from gpu_util import RHO_TOL, assert_rho_close, entry_weights_f64, jaccard, lib, rho_error
 
 pytestmark = pytest.mark.gpu
 
@@ -188,7 +188,10 @@ def test_batched_graphs_match_each_graph_alone(storage):
         part = rho[eoff[k]:eoff[k + 1]]
         if storage == "fp32":
             assert_rho_close(part, oracle.algebraic_distance(gg.row_ptr, gg.col, None, R=16, k=15, omega=0.5, seed=7))
-        np.testing.assert_array_equal(part, r1)      # same kernels, same arithmetic
+        # same kernels; the streaming sweep cuts rows at other places in the batch than
+        # alone, so the two differ only in the order of FP32 additions (and, with 16-bit
+        # storage, in the roundings that order can flip)
+        assert rho_error(part, r1.astype(np.float64)) <= (RHO_TOL if storage == "fp32" else 0.05)
     # per-graph sparsification targets on identical scores
     s = graphgen.random_scores(big.m, 30, seed=5)
     for scope in ("whole_graph", "per_node"):
