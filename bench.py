@@ -145,16 +145,27 @@ def algorithmic_bytes_per_sweep(g, storage):
     return g.nnz * 4 + (g.n + 1) * 4 + g.n * 4 + 2 * n_active * R * s, n_active
 
 
-def cpu_baseline(g, budget_s=20.0):
-    """The FP64 oracle as it stands (single-threaded C) on a bounded sample:
-    the full graph with R = 32 test vectors and one JOR sweep."""
+def cpu_baseline(g):
+    """The FP64 oracle as it stands on a bounded sample of the workload (the full
+    graph, R = 32, k sweeps), on one host core and with its row loops on all host
+    cores (OpenMP over rows, the per-row arithmetic unchanged), seconds per phase."""
     import oracle
-    k = 1
-    t0 = time.perf_counter()
-    oracle.algebraic_distance(g.row_ptr, g.col, None, R=R, k=k, omega=OMEGA, seed=SEED)
-    dt = time.perf_counter() - t0
-    return {"value": g.nnz * R * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"same R-MAT scale-{SCALE} graph, R={R}, k={k} sweep (+ init and distance), FP64, {dt:.1f} s"}
+    cores = os.cpu_count() or 1
+    out = {}
+    for label, threads, k in (("one_core", 1, 1), ("all_cores", cores, 4)):
+        oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        oracle.algebraic_distance(g.row_ptr, g.col, None, R=R, k=k, omega=OMEGA, seed=SEED)
+        dt = time.perf_counter() - t0
+        out[label] = {"value": g.nnz * R * k / dt, "threads": oracle.max_threads(), "k": k, "seconds": dt,
+                      "phase_seconds": oracle.last_phase_seconds()}
+    oracle.set_threads(cores)
+    best = out["all_cores"]
+    return {"value": best["value"], "unit": UNIT, "cores": best["threads"], "kind": "oracle",
+            "sample": f"same R-MAT scale-{SCALE} graph, R={R}, FP64; one core: k=1 sweep "
+                      f"({out['one_core']['seconds']:.1f} s); all cores: k=4 sweeps ({best['seconds']:.1f} s), "
+                      "each + init and distance",
+            "runs": out}
 
 
 def run_reference(args):
@@ -164,6 +175,7 @@ def run_reference(args):
     g = make_graph()
     import oracle
     oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
     k = 1
     times = []
     for it in range(args.warmup + args.steps):
@@ -179,8 +191,9 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload(), "sample": f"each step: FP64 oracle, R={R}, k={k} sweep on the full graph",
                        "n": g.n, "m": g.m, "nnz": g.nnz},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"R={R}, k={k} sweep (+ init and distance) on the full graph per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"R={R}, k={k} sweep (+ init and distance) on the full graph per step, "
+                                       "row loops on all host cores"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -373,6 +386,11 @@ def run_gpu(args):
                 "storage_variants": variants or None,
                 "sparsify_binned": binned,
                 "clocks": clk}
+        if ws == 1 and args.workloads:
+            line["workloads"] = {}
+            for name, fn in WORKLOADS.items():
+                kw = {} if name in ("grid64", "rmat22") else {"storage": "bf16" if name == "ws512" else "fp32"}
+                line["workloads"][name] = fn(L, dev, stream, min(args.steps, 3), max(args.warmup, 3), **kw)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g)
         print(json.dumps(line), flush=True)
@@ -382,124 +400,206 @@ def run_gpu(args):
     return 0
 
 
-def run_workload(args):
-    """The other workloads of the hot path, one JSON line each (not the headline):
-    ws512  -- 512 Watts-Strogatz graphs (n ~ U{1000..200000}, ring degree 10, p = 0.1) in one
-              batched handle, R = 16, k = 15, 16-bit storage, per-graph 25% global per-node
-              sparsification; compared with the plain form (FP32, one handle per graph);
-    ba2m   -- multilevel (Alg. 6) on Barabasi-Albert n = 2,000,000, m = 8, lognormal weights,
-              R = 16, k = 20, hierarchy to about 1,000 vertices, 40% at the coarse levels;
-    rmat22 -- reverse mode: R-MAT scale 22 with uniform(0.5, 2) weights, R = 32, k = 30,
-              loss over a seeded 1% edge subset, forward with checkpoints + backward."""
+def _timed(stream, fn, steps, warmup, mark=True):
     import torch
-    from paper_1601_05527_gb300 import build, graphgen, _lib as L
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if mark:
+        torch.cuda.nvtx.range_push("timed_steps")     # lets a profiler pick out the timed launches
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    if mark:
+        torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _sweep_ms(L, h, fn, runs=2):
+    """Average event time of one JOR sweep launch of handle h over `runs` calls of fn."""
+    L.ad_graph_set_profiling(h, True)
+    L.ad_graph_phase_time(h, "sweep", reset=True)
+    for _ in range(runs):
+        fn()
+    ms, cnt = L.ad_graph_phase_time(h, "sweep", reset=True)
+    L.ad_graph_set_profiling(h, False)
+    return ms / max(cnt, 1)
+
+
+def _roofline(b_sweep, sweep_ms, what):
+    peak, kind = measured_peaks()
+    ach = b_sweep / (sweep_ms / 1e3) / 1e9
+    return {"kernel": what, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": kind, "algorithmic_bytes_per_launch": b_sweep, "avg_launch_ms": sweep_ms}
+
+
+def sweep_bytes(n, nnz, n_active, R_, s, weighted):
+    """Algorithmic bytes of one sweep (gathers assumed on chip): column indices,
+    row pointers, inverse degrees, weights if any, one read + one write of
+    every active row of the R-wide block."""
+    return nnz * 4 + (n + 1) * 4 + n * 4 + (nnz * 4 if weighted else 0) + 2 * n_active * R_ * s
+
+
+def workload_grid64(L, dev, stream, steps, warmup):
+    """2-D 64x64 grid, unit weights, R = 8, k = 20, 50% by global whole-graph ranking:
+    a latency-bound case, reported in microseconds per call."""
+    import torch
+    from paper_1601_05527_gb300 import graphgen
+    g = graphgen.grid2d(64, 64)
+    h = L.ad_graph_create(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev), None, 0, stream)
+    keep = torch.empty(g.m, dtype=torch.uint8, device=dev)
+
+    def ad():
+        L.ad_algebraic_distance(h, 8, 20, OMEGA, SEED, 0, "fp32", 0, None)
+
+    def step():
+        ad()
+        L.ad_sparsify(h, 0.5, "global", "whole_graph", keep)
+    reps = max(20, steps * 10)
+    ms_ad = _timed(stream, ad, reps, max(warmup, 3), mark=False)
+    ms = _timed(stream, step, reps, max(warmup, 3), mark=False)
+    L.ad_graph_destroy(h)
+    units = g.nnz * 8 * 20
+    return {"workload": "2-D grid 64x64 (4,096 vertices, 8,064 edges), unit weights, R=8, k=20, omega=0.5, "
+                        "50% by global whole-graph ranking",
+            "distance_us": 1e3 * ms_ad, "step_us": 1e3 * ms, "value": units / (ms / 1e3), "unit": UNIT,
+            "note": "latency-bound: microseconds per call, repeated calls replay a recorded CUDA graph"}
+
+
+def workload_ws512(L, dev, stream, steps, warmup, storage="bf16"):
+    """512 Watts-Strogatz graphs in one batched handle, R = 16, k = 15, 16-bit storage,
+    per-graph 25% global per-node sparsification; against the plain FP32 form with
+    one handle per graph."""
+    import torch
+    from paper_1601_05527_gb300 import graphgen
+    st = storage if storage != "fp32" else "bf16"
+    graphs = graphgen.ws_batch(512, seed=5)
+    voff, big = graphgen.concat(graphs)
+    h = L.ad_graph_create_batched(voff, big.n, torch.from_numpy(big.row_ptr).to(dev),
+                                  torch.from_numpy(big.col).to(dev), None, 0, stream)
+    keep = torch.empty(big.m, dtype=torch.uint8, device=dev)
+
+    def ad():
+        L.ad_algebraic_distance(h, 16, 15, OMEGA, SEED, 0, st, 0, None)
+
+    def step():
+        ad()
+        L.ad_sparsify(h, 0.25, "global", "per_node", keep)
+    ms = _timed(stream, step, steps, warmup)
+    sw = _sweep_ms(L, h, ad)
+    L.ad_graph_destroy(h)
+    hs = [L.ad_graph_create(gg.n, torch.from_numpy(gg.row_ptr).to(dev), torch.from_numpy(gg.col).to(dev), None,
+                            0, stream) for gg in graphs]
+    keeps = [torch.empty(gg.m, dtype=torch.uint8, device=dev) for gg in graphs]
+
+    def plain():
+        for hh, kk in zip(hs, keeps):
+            L.ad_algebraic_distance(hh, 16, 15, OMEGA, SEED, 0, "fp32", 0, None)
+            L.ad_sparsify(hh, 0.25, "global", "per_node", kk)
+    ms_plain = _timed(stream, plain, 1, 1, mark=False)
+    for hh in hs:
+        L.ad_graph_destroy(hh)
+    units = big.nnz * 16 * 15
+    return {"workload": "512 Watts-Strogatz graphs, n ~ U{1000..200000}, ring degree 10, p=0.1, R=16, k=15, "
+                        "per-graph 25% global per-node sparsification, one batched handle",
+            "n": big.n, "m": big.m, "nnz": big.nnz, "storage": st, "value": units / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms,
+            "roofline": _roofline(sweep_bytes(big.n, big.nnz, big.n, 16, 2, False), sw,
+                                  "k_sweep_stream (one JOR sweep of the whole batch)"),
+            "plain_fp32_one_handle_per_graph": {"value": units / (ms_plain / 1e3), "ms_per_step": ms_plain}}
+
+
+def workload_ba2m(L, dev, stream, steps, warmup, storage="fp32"):
+    """Multilevel Alg. 6 on Barabasi-Albert n = 2,000,000, m = 8, lognormal weights,
+    R = 16, k = 20, hierarchy to about 1,000 vertices, 40% controlled at the coarse
+    third of the levels, through the one-shot call."""
+    import torch
+    from paper_1601_05527_gb300 import graphgen
+    g = graphgen.barabasi_albert(2_000_000, 8, seed=4)
+    g = graphgen.with_edge_weights(g, graphgen.lognormal_edge_weights(g.m, seed=4))
+    h = L.ad_graph_create(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                          torch.from_numpy(g.weight).to(dev), 0, stream)
+    keep = torch.empty(g.m, dtype=torch.uint8, device=dev)
+    params = dict(R=16, k=20, omega=OMEGA, seed=SEED, Q=0.5, coarsest_n=1000, mode="local", storage=storage)
+    ml = L.ad_ml_build(h, **params)
+    lv = L.ad_ml_levels(ml)
+    sizes = [L.ad_ml_level_size(ml, l) for l in range(lv)]
+    L.ad_ml_destroy(ml)
+    ratios = L.ad_ml_segment_ratios(lv, "coarse", max(1, lv // 3), 1.0)[:max(1, lv // 3)]
+
+    def step():
+        L.ad_multilevel(h, ratios, 0.4, keep, **params)
+    ms = _timed(stream, step, steps, warmup)
+    kept = int(keep.sum())
+    sw = _sweep_ms(L, h, lambda: L.ad_algebraic_distance(h, 16, 20, OMEGA, SEED, 0, storage, 0, None))
+    L.ad_graph_destroy(h)
+    units = sum(2 * m_l for _, m_l in sizes) * 16 * 20    # the sweeps of the downward pass
+    return {"workload": "multilevel Alg. 6: Barabasi-Albert n=2,000,000 m=8, lognormal(0,1) weights, R=16, k=20, "
+                        "Q=0.5, coarsest 1000, 40% controlled at the coarse third of levels (ad_multilevel)",
+            "levels": [list(x) for x in sizes], "kept": kept, "value": units / (ms / 1e3), "unit": UNIT,
+            "units": "sum over levels of nnz_l*R*k of the downward pass", "ms_per_step": ms,
+            "roofline": _roofline(sweep_bytes(g.n, g.nnz, int((g.degrees() > 0).sum()), 16,
+                                              4 if storage == "fp32" else 2, True), sw,
+                                  "k_sweep_stream (one JOR sweep of the finest level)")}
+
+
+def workload_rmat22(L, dev, stream, steps, warmup):
+    """Reverse mode: R-MAT scale 22 with uniform(0.5, 2) weights, R = 32, k = 30, loss
+    over a seeded 1% edge subset, forward with checkpoints + backward."""
+    import torch
+    from paper_1601_05527_gb300 import graphgen
+    g = graphgen.rmat(22, 16, seed=6)
+    ew = graphgen.uniform_edge_weights(g.m, seed=6)
+    g = graphgen.with_edge_weights(g, ew)
+    S = torch.from_numpy(graphgen.random_edge_subset(g.m, 0.01, seed=6)).to(dev)
+    h = L.ad_graph_create(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                          torch.from_numpy(g.weight).to(dev), 0, stream)
+    rho = torch.empty(g.m, dtype=torch.float32, device=dev)
+    rb = torch.zeros(g.m, dtype=torch.float32, device=dev)
+    wb = torch.empty(g.m, dtype=torch.float32, device=dev)
+
+    def fwd():
+        L.ad_algebraic_distance(h, 32, 30, OMEGA, SEED, 0, "fp32", L.AD_DIST_KEEP_STATE, rho)
+
+    def step():
+        fwd()
+        rb.index_copy_(0, S, 2.0 * rho.index_select(0, S))
+        L.ad_algebraic_distance_backward(h, rb, wb)
+    ms_fwd = _timed(stream, fwd, steps, warmup, mark=False)
+    ms = _timed(stream, step, steps, warmup)
+    sw = _sweep_ms(L, h, lambda: L.ad_algebraic_distance(h, 32, 30, OMEGA, SEED, 0, "fp32", 0, None))
+    L.ad_graph_destroy(h)
+    units = g.nnz * 32 * 30
+    return {"workload": "reverse mode: R-MAT scale 22, uniform(0.5,2) weights, R=32, k=30, "
+                        "loss = sum of rho^2 over a seeded 1% edge subset, sqrt(k) checkpoints",
+            "n": g.n, "m": g.m, "nnz": g.nnz, "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "forward_with_checkpoints_ms": ms_fwd, "backward_ms": ms - ms_fwd,
+            "roofline": _roofline(sweep_bytes(g.n, g.nnz, int((g.degrees() > 0).sum()), 32, 4, True), sw,
+                                  "k_sweep_stream (one forward JOR sweep)")}
+
+
+WORKLOADS = {"grid64": workload_grid64, "ws512": workload_ws512, "ba2m": workload_ba2m, "rmat22": workload_rmat22}
+
+
+def run_workload(args):
+    """One of the other workloads of the hot path on its own, one JSON line."""
+    import torch
+    from paper_1601_05527_gb300 import build, _lib as L
     build.build()
     L.load()
     L.use_torch_allocator()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
-
-    def timed(fn, steps, warmup, mark=True):
-        for _ in range(warmup):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if mark:
-            torch.cuda.nvtx.range_push("timed_steps")     # lets a profiler pick out the timed launches
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        if mark:
-            torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
-
+    fn = WORKLOADS[args.workload]
+    kw = {} if args.workload in ("grid64", "rmat22") else {"storage": args.storage}
+    res = fn(L, dev, stream, args.steps, args.warmup, **kw)
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
-    if args.workload == "ws512":
-        st = args.storage if args.storage != "fp32" else "bf16"
-        graphs = graphgen.ws_batch(512, seed=5)
-        voff, big = graphgen.concat(graphs)
-        h = L.ad_graph_create_batched(voff, big.n, torch.from_numpy(big.row_ptr).to(dev),
-                                      torch.from_numpy(big.col).to(dev), None, 0, stream)
-        keep = torch.empty(big.m, dtype=torch.uint8, device=dev)
-
-        def step():
-            L.ad_algebraic_distance(h, 16, 15, OMEGA, SEED, 0, st, 0, None)
-            L.ad_sparsify(h, 0.25, "global", "per_node", keep)
-        ms = timed(step, args.steps, args.warmup)
-        L.ad_graph_destroy(h)
-        hs = [L.ad_graph_create(gg.n, torch.from_numpy(gg.row_ptr).to(dev), torch.from_numpy(gg.col).to(dev), None,
-                                0, stream) for gg in graphs]
-        keeps = [torch.empty(gg.m, dtype=torch.uint8, device=dev) for gg in graphs]
-
-        def plain():
-            for hh, kk in zip(hs, keeps):
-                L.ad_algebraic_distance(hh, 16, 15, OMEGA, SEED, 0, "fp32", 0, None)
-                L.ad_sparsify(hh, 0.25, "global", "per_node", kk)
-        ms_plain = timed(plain, max(1, args.steps // 5), 1, mark=False)
-        for hh in hs:
-            L.ad_graph_destroy(hh)
-        units = big.nnz * 16 * 15
-        line.update({"value": units / (ms / 1e3), "ms_per_step": ms, "dtype": f"{st} storage, f32 accumulate",
-                     "config": {"workload": "512 Watts-Strogatz graphs, n ~ U{1000..200000}, ring degree 10, p=0.1, "
-                                            "R=16, k=15, per-graph 25% global per-node sparsification, one batched handle",
-                                "n": big.n, "m": big.m, "nnz": big.nnz, "storage": st},
-                     "plain_fp32_one_handle_per_graph": {"value": units / (ms_plain / 1e3), "ms_per_step": ms_plain}})
-    elif args.workload == "ba2m":
-        g = graphgen.barabasi_albert(2_000_000, 8, seed=4)
-        g = graphgen.with_edge_weights(g, graphgen.lognormal_edge_weights(g.m, seed=4))
-        h = L.ad_graph_create(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
-                              torch.from_numpy(g.weight).to(dev), 0, stream)
-        keep = torch.empty(g.m, dtype=torch.uint8, device=dev)
-        info = {}
-
-        def step():
-            ml = L.ad_ml_build(h, R=16, k=20, omega=OMEGA, seed=SEED, Q=0.5, coarsest_n=1000, mode="local",
-                               storage=args.storage)
-            lv = L.ad_ml_levels(ml)
-            ratios = L.ad_ml_segment_ratios(lv, "coarse", max(1, lv // 3), 1.0)
-            info["kept"], info["r"] = L.ad_ml_sparsify(ml, ratios, 0.4, keep)
-            info["sizes"] = [L.ad_ml_level_size(ml, l) for l in range(lv)]
-            L.ad_ml_destroy(ml)
-        ms = timed(step, args.steps, args.warmup)
-        L.ad_graph_destroy(h)
-        units = sum(2 * m_l for _, m_l in info["sizes"]) * 16 * 20    # the sweeps of the downward pass
-        line.update({"value": units / (ms / 1e3), "ms_per_step": ms, "dtype": "f32" if args.storage == "fp32" else
-                     f"{args.storage} storage, f32 accumulate",
-                     "config": {"workload": "multilevel Alg. 6: Barabasi-Albert n=2,000,000 m=8, lognormal(0,1) weights, "
-                                            "R=16, k=20, Q=0.5, coarsest 1000, 40% controlled at the coarse third of levels",
-                                "levels": [list(x) for x in info["sizes"]], "kept": info["kept"], "ratio": info["r"],
-                                "units": "sum over levels of nnz_l*R*k of the downward pass"}})
-    elif args.workload == "rmat22":
-        g = graphgen.rmat(22, 16, seed=6)
-        ew = graphgen.uniform_edge_weights(g.m, seed=6)
-        g = graphgen.with_edge_weights(g, ew)
-        S = torch.from_numpy(graphgen.random_edge_subset(g.m, 0.01, seed=6)).to(dev)
-        h = L.ad_graph_create(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
-                              torch.from_numpy(g.weight).to(dev), 0, stream)
-        rho = torch.empty(g.m, dtype=torch.float32, device=dev)
-        rb = torch.zeros(g.m, dtype=torch.float32, device=dev)
-        wb = torch.empty(g.m, dtype=torch.float32, device=dev)
-
-        def fwd():
-            L.ad_algebraic_distance(h, 32, 30, OMEGA, SEED, 0, "fp32", L.AD_DIST_KEEP_STATE, rho)
-
-        def step():
-            fwd()
-            rb.index_copy_(0, S, 2.0 * rho.index_select(0, S))
-            L.ad_algebraic_distance_backward(h, rb, wb)
-        ms_fwd = timed(fwd, args.steps, args.warmup, mark=False)
-        ms = timed(step, args.steps, args.warmup)
-        L.ad_graph_destroy(h)
-        units = g.nnz * 32 * 30
-        line.update({"value": units / (ms / 1e3), "ms_per_step": ms, "dtype": "f32",
-                     "config": {"workload": "reverse mode: R-MAT scale 22, uniform(0.5,2) weights, R=32, k=30, "
-                                            "loss = sum of rho^2 over a seeded 1% edge subset, sqrt(k) checkpoints",
-                                "n": g.n, "m": g.m, "nnz": g.nnz},
-                     "forward_with_checkpoints_ms": ms_fwd, "backward_ms": ms - ms_fwd})
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "value": res.pop("value"), "config": {"workload": res.pop("workload")}, **res}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -515,8 +615,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the 16-bit storage comparison")
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "ws512", "ba2m", "rmat22"],
-                    help="rmat20 is the benchmark; the others time the batched, multilevel and reverse-mode paths")
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "grid64", "ws512", "ba2m", "rmat22"],
+                    help="rmat20 is the benchmark; the others time the latency-bound, batched, multilevel and "
+                         "reverse-mode paths (the default line carries them too)")
+    ap.add_argument("--no-workloads", dest="workloads", action="store_false",
+                    help="leave the other workloads out of the default line")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT scale; values other than 20 are smaller profiling cases, not the benchmark")
     args = ap.parse_args()
