@@ -508,7 +508,7 @@ def workload_ws512(L, dev, stream, steps, warmup, storage="bf16"):
             "n": big.n, "m": big.m, "nnz": big.nnz, "storage": st, "value": units / (ms / 1e3), "unit": UNIT,
             "ms_per_step": ms,
             "roofline": _roofline(sweep_bytes(big.n, big.nnz, big.n, 16, 2, False), sw,
-                                  "k_sweep_stream (one JOR sweep of the whole batch)"),
+                                  "k_sweep (one JOR sweep of the whole batch)"),
             "plain_fp32_one_handle_per_graph": {"value": units / (ms_plain / 1e3), "ms_per_step": ms_plain}}
 
 
@@ -543,7 +543,7 @@ def workload_ba2m(L, dev, stream, steps, warmup, storage="fp32"):
             "units": "sum over levels of nnz_l*R*k of the downward pass", "ms_per_step": ms,
             "roofline": _roofline(sweep_bytes(g.n, g.nnz, int((g.degrees() > 0).sum()), 16,
                                               4 if storage == "fp32" else 2, True), sw,
-                                  "k_sweep_stream (one JOR sweep of the finest level)")}
+                                  "k_sweep (one JOR sweep of the finest level)")}
 
 
 def workload_rmat22(L, dev, stream, steps, warmup):
@@ -578,7 +578,7 @@ def workload_rmat22(L, dev, stream, steps, warmup):
             "n": g.n, "m": g.m, "nnz": g.nnz, "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "forward_with_checkpoints_ms": ms_fwd, "backward_ms": ms - ms_fwd,
             "roofline": _roofline(sweep_bytes(g.n, g.nnz, int((g.degrees() > 0).sum()), 32, 4, True), sw,
-                                  "k_sweep_stream (one forward JOR sweep)")}
+                                  "k_sweep (one forward JOR sweep)")}
 
 
 WORKLOADS = {"grid64": workload_grid64, "ws512": workload_ws512, "ba2m": workload_ba2m, "rmat22": workload_rmat22}

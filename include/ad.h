@@ -271,13 +271,12 @@ ad_status ad_select_per_node(ad_graph_t g, const float *score, double e, ad_mode
 
 /*
  * Picks the launch shape of the JOR sweep (Alg. 1) for this graph, R and
- * storage by timing the candidates on the handle: resident CTAs per SM of the
- * streaming sweep (as many as fit, and 2), which also sets how many equal
- * ranges of CSR entries the sweep is cut into.  Each candidate runs a short
+ * storage by timing the candidates on the handle: lanes per row (the natural
+ * 16-byte-chunk layout, and half as many lanes with two chunks each) x
+ * resident CTAs per SM (as many as fit, 5, 4).  Each candidate runs a short
  * distance computation (k = 4) three times; the fastest shape is kept on the
  * handle and used by every later call with this R and storage.  The result
- * depends on the shape only through the order of FP32 additions (where the
- * ranges cut rows).
+ * depends only on the shape through the order of FP32 additions.
  *   lanes_per_row, chunks_per_lane, ctas_per_sm (0 = as many as fit): the
  *   chosen shape; each may be NULL.
  * Errors: AD_ERR_INVALID_ARG, AD_ERR_OOM, AD_ERR_CUDA.

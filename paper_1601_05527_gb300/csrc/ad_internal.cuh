@@ -215,15 +215,6 @@ struct DevBuf {
 constexpr int kChunk = AD_CHUNK;
 constexpr int kBig = AD_CHUNK;
 
-// Plan of the streaming sweep (k_sweep_stream): for S ranges of equal length of
-// the long rows' entries, the first row of each range and the split-row counters.
-struct StreamPlan {
-    int32_t S_req = 0;              // range count asked for
-    int32_t S = 0;                  // ranges used (fewer on small graphs)
-    int32_t *k0 = nullptr;          // [S]
-    uint32_t *counter = nullptr;    // [S], zero between launches
-};
-
 struct RowPlan {
     int small_max = 0;          // degree bound of the small class
     int groups = 0;             // lane groups per warp the plan was built for
@@ -276,12 +267,6 @@ struct ad_graph_s {
 
     // work plans keyed by lane-group count
     std::vector<ad::RowPlan> sweep_plans, dist_plans;
-    // streaming sweep (built once): long rows with their sequence and CSR begins, short rows
-    // as (row, CSR begin, degree, 0); plans keyed by the requested range count
-    int32_t *lrow = nullptr, *lbeg = nullptr, *lcsr = nullptr, *srows = nullptr;
-    int64_t n_long = 0, n_short = 0, nnz_long = 0;
-    bool have_stream_rows = false;
-    std::vector<ad::StreamPlan> stream_plans;
 
     // scores of the last ad_algebraic_distance call
     float *rho = nullptr;
@@ -372,7 +357,6 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
 ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, const void *x_in, void *x_out,
                      const uint32_t *pmin, const uint32_t *pmax, uint32_t *mn, uint32_t *mx);
 ad_status get_row_plan(ad_graph_t g, int groups, bool upper, RowPlan **out);
-ad_status get_stream_plan(ad_graph_t g, int32_t S, StreamPlan **out);   // sweep.cu
 void natural_shape(int R, ad_storage storage, int *lanes_per_row, int *chunks_per_lane);   // sweep.cu
 
 // selection (select.cu)

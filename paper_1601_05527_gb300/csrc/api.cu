@@ -439,7 +439,10 @@ extern "C" ad_status ad_graph_autotune(ad_graph_t g, int32_t R, ad_storage stora
     natural_shape(R, storage, &nat_lpr, &nat_cpl);
     struct Cand { int lpr, cpl, per_sm; };
     std::vector<Cand> cands;
-    for (int per_sm : {0, 2}) cands.push_back({nat_lpr, nat_cpl, per_sm});
+    std::vector<std::pair<int, int>> shapes = {{nat_lpr, nat_cpl}};
+    if (nat_lpr >= 2 && nat_cpl == 1) shapes.push_back({nat_lpr / 2, 2});
+    for (const auto &sh : shapes)
+        for (int per_sm : {0, 5, 4}) cands.push_back({sh.first, sh.second, per_sm});
     int best = 0;
     float best_ms = 0.f;
     if (g->m > 0) {

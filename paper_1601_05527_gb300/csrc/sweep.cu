@@ -65,104 +65,6 @@ static ad_status dispatch_storage(ad_graph_t g, ad_storage storage, const Config
     }
 }
 
-// ----------------------------------------------------------------------------
-// Streaming-sweep plan: long rows (degree > kShortMax) with the position of
-// their first entry in the long rows' sequence and in the CSR, short rows as
-// (row, CSR begin, degree), and the first long row of each of S ranges.
-// ----------------------------------------------------------------------------
-__global__ void k_row_kinds(const int64_t *rp, int64_t n, uint8_t *is_long, uint8_t *is_short, int64_t *ldeg) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t d = rp[i + 1] - rp[i];
-        is_long[i] = d > kShortMax ? 1 : 0;
-        is_short[i] = (d > 0 && d <= kShortMax) ? 1 : 0;
-        ldeg[i] = d > kShortMax ? d : 0;
-    }
-}
-
-__global__ void k_long_fill(const int64_t *idx, int64_t nl, const int64_t *rp, const int64_t *lpos, int32_t *lrow,
-                            int32_t *lbeg, int32_t *lcsr) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx[k];
-        lrow[k] = (int32_t)i;
-        lbeg[k] = (int32_t)lpos[i];
-        lcsr[k] = (int32_t)rp[i];
-    }
-}
-
-__global__ void k_short_fill(const int64_t *idx, int64_t ns, const int64_t *rp, int4 *srows) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ns; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx[k];
-        srows[k] = make_int4((int32_t)i, (int32_t)rp[i], (int32_t)(rp[i + 1] - rp[i]), 0);
-    }
-}
-
-// k0[s] = the first long row whose entries reach past the first entry of range s
-__global__ void k_range_first_row(const int32_t *lbeg, int64_t nl, int32_t S, int64_t len, int32_t *k0) {
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = s * len / S;
-        int64_t lo = 0, hi = nl;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)lbeg[mid + 1] > b) hi = mid; else lo = mid + 1;
-        }
-        k0[s] = (int32_t)lo;
-    }
-}
-
-static ad_status stream_rows(ad_graph_t g) {
-    if (g->have_stream_rows) return AD_OK;
-    const int64_t n = g->n;
-    uint8_t *fl = nullptr, *fs = nullptr;
-    int64_t *ldeg = nullptr, *lpos = nullptr, *il = nullptr, *is = nullptr, nl = 0, ns = 0, nnz_long = 0;
-    AD_TRY(dalloc_t(g, n + 1, &fl));
-    AD_TRY(dalloc_t(g, n + 1, &fs));
-    AD_TRY(dalloc_t(g, n + 1, &ldeg));
-    AD_TRY(dalloc_t(g, n + 1, &lpos));
-    if (n > 0) AD_LAUNCH(k_row_kinds, g->num_sms * 8, 256, 0, g->stream, g->rp, n, fl, fs, ldeg);
-    AD_TRY(exclusive_scan_i64(g, ldeg, lpos, n, &nnz_long));
-    AD_TRY(compact_flags(g, fl, n, &il, &nl));
-    AD_TRY(compact_flags(g, fs, n, &is, &ns));
-    AD_TRY(dalloc_t(g, nl + 1, &g->lrow));
-    AD_TRY(dalloc_t(g, nl + 1, &g->lbeg));
-    AD_TRY(dalloc_t(g, nl + 1, &g->lcsr));
-    AD_TRY(dalloc_t(g, 4 * (ns + 1), &g->srows));
-    if (nl > 0) AD_LAUNCH(k_long_fill, g->num_sms * 8, 256, 0, g->stream, il, nl, g->rp, lpos, g->lrow, g->lbeg, g->lcsr);
-    const int32_t end32 = (int32_t)nnz_long;
-    AD_CUDA_TRY(cudaMemcpyAsync(g->lbeg + nl, &end32, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
-    if (ns > 0)
-        AD_LAUNCH(k_short_fill, g->num_sms * 8, 256, 0, g->stream, is, ns, g->rp, reinterpret_cast<int4 *>(g->srows));
-    AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    for (void *b : {(void *)fl, (void *)fs, (void *)ldeg, (void *)lpos, (void *)il, (void *)is})
-        if (b) dfree(g, b);
-    g->n_long = nl;
-    g->n_short = ns;
-    g->nnz_long = nnz_long;
-    g->have_stream_rows = true;
-    return AD_OK;
-}
-
-ad_status get_stream_plan(ad_graph_t g, int32_t S_req, StreamPlan **out) {
-    for (auto &p : g->stream_plans)
-        if (p.S_req == S_req) { *out = &p; return AD_OK; }
-    AD_TRY(stream_rows(g));
-    StreamPlan p;
-    p.S_req = S_req;
-    int64_t S = S_req;
-    const int64_t smax = g->nnz_long / 32;   // ranges of at least 32 entries
-    if (S > smax) S = smax;
-    if (S < 1) S = 1;
-    p.S = (int32_t)S;
-    AD_TRY(dalloc_t(g, S, &p.k0));
-    AD_TRY(dalloc_t(g, S, &p.counter));
-    AD_CUDA_TRY(cudaMemsetAsync(p.counter, 0, (size_t)S * sizeof(uint32_t), g->stream));
-    if (g->n_long > 0)
-        AD_LAUNCH(k_range_first_row, (int)((S + 255) / 256), 256, 0, g->stream, g->lbeg, g->n_long, (int32_t)S,
-                  g->nnz_long, p.k0);
-    g->stream_plans.push_back(p);
-    *out = &g->stream_plans.back();
-    return AD_OK;
-}
-
 ad_status get_row_plan(ad_graph_t g, int groups, bool upper, RowPlan **out);
 static ad_status get_plan(ad_graph_t g, int groups, bool upper, RowPlan **out) { return get_row_plan(g, groups, upper, out); }
 ad_status get_row_plan(ad_graph_t g, int groups, bool upper, RowPlan **out) {
@@ -201,16 +103,21 @@ static void ev_end(ad_graph_t g, double &acc, int64_t &cnt) {
 ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, const void *x_in, void *x_out,
                      const uint32_t *pmin, const uint32_t *pmax, uint32_t *mn, uint32_t *mx) {
     const Config cf = pick_config(g, R, storage);
+    RowPlan *sp = nullptr;
+    AD_TRY(get_plan(g, 32 / cf.lpr, false, &sp));
+    AD_TRY(ensure(g, g->part, (size_t)(sp->n_big > 0 ? sp->n_big : 1) * cf.stride * sizeof(float)));
     SweepArgs a;
     memset(&a, 0, sizeof(a));
     a.rp = g->rp; a.col = g->col; a.w = g->w; a.Dinv = g->Dinv; a.D = g->D;
     a.upos = g->upos; a.eoff = g->eoff;
+    a.part = static_cast<float *>(g->part.ptr);
     a.stride = cf.stride; a.nchunks = cf.nchunks; a.R = R;
     a.omega = (float)omega;
     a.voff = g->voff; a.G = g->G; a.blocked = g->G > 1 ? 1 : 0;
     a.anchor = g->anchor;
     AD_TRY(ensure(g, g->ac, (size_t)g->G * 2 * cf.stride * sizeof(float)));
     a.ac = static_cast<float *>(g->ac.ptr);
+    fill_plan(a, *sp);
     a.x_in = x_in; a.x_out = x_out;
     a.mm_prev_min = pmin; a.mm_prev_max = pmax; a.mm_min = mn; a.mm_max = mx;
     return dispatch_storage(g, storage, cf, true, a, 2 * 8 * (size_t)cf.stride * sizeof(float));
@@ -233,8 +140,10 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
     AD_CUDA_TRY(cudaMemsetAsync(mm_min, 0xff, mm_words * sizeof(uint32_t), g->stream));
     AD_CUDA_TRY(cudaMemsetAsync(mm_max, 0x00, mm_words * sizeof(uint32_t), g->stream));
 
-    RowPlan *dp = nullptr;
+    RowPlan *sp = nullptr, *dp = nullptr;
+    AD_TRY(get_plan(g, groups, false, &sp));
     AD_TRY(get_plan(g, groups, true, &dp));
+    AD_TRY(ensure(g, g->part, (size_t)(sp->n_big > 0 ? sp->n_big : 1) * cf.stride * sizeof(float)));
 
     // init
     {
@@ -254,6 +163,7 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
     memset(&a, 0, sizeof(a));
     a.rp = g->rp; a.col = g->col; a.w = g->w; a.Dinv = g->Dinv; a.D = g->D;
     a.upos = g->upos; a.eoff = g->eoff;
+    a.part = static_cast<float *>(g->part.ptr);
     a.stride = cf.stride; a.nchunks = cf.nchunks; a.R = R;
     a.omega = (float)omega;
     a.normalize = (flags & AD_DIST_NORMALIZE) ? 1 : 0;
@@ -266,6 +176,7 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
 
     void *xin = g->x0.ptr, *xout = g->x1.ptr;
     const size_t smem = 2 * 8 * (size_t)cf.stride * sizeof(float);
+    fill_plan(a, *sp);
     for (int32_t t = 0; t < k; ++t) {
         a.x_in = xin; a.x_out = xout;
         const size_t slot = (size_t)g->G * cf.stride;

@@ -27,16 +27,13 @@
 
 // Tuning parameters (compile-time; the defaults are the measured choice on GB300).
 #ifndef AD_SWEEP_UB
-#define AD_SWEEP_UB 4          // independent row loads in flight per lane of the distance pass
+#define AD_SWEEP_UB 4          // independent row loads in flight per lane
 #endif
-#ifndef AD_STREAM_U32
-#define AD_STREAM_U32 8        // row loads in flight per lane of the streaming sweep, FP32 rows
+#ifndef AD_SWEEP_MINB
+#define AD_SWEEP_MINB 6        // resident CTAs per SM requested from ptxas for the FP32 sweep
 #endif
-#ifndef AD_STREAM_U16
-#define AD_STREAM_U16 4        // ... 16-bit rows
-#endif
-#ifndef AD_STREAM_MINB
-#define AD_STREAM_MINB 3       // resident CTAs per SM requested from ptxas for the streaming sweep
+#ifndef AD_SWEEP_MINB16
+#define AD_SWEEP_MINB16 5      // ... for the 16-bit storage formats
 #endif
 #ifndef AD_DIST_MINB
 #define AD_DIST_MINB 4         // ... for the distance pass
@@ -69,6 +66,7 @@ struct SweepArgs {
     const int64_t *eoff;   // distance: edge id of that entry
     const void *x_in;
     void *x_out;
+    float *part;           // [n_big][stride] partial sums of big rows
     const uint32_t *mm_prev_min, *mm_prev_max;  // nullptr at t = 0
     uint32_t *mm_min, *mm_max;                  // this sweep's min/max
     float *rho;            // distance output
@@ -90,21 +88,6 @@ struct SweepArgs {
     int32_t blocked;
     const int32_t *anchor;   // [G] vertex whose previous value is subtracted (the stored frame's centre)
     float *ac;               // [G][2][stride]: scale a and centre c of this sweep (k_scale_center)
-    // streaming sweep (k_sweep_stream).  Long rows (degree > kShortMax): their
-    // entries, row after row, form a sequence [0, nnz_long) cut into S ranges of
-    // equal length, range s = [s nnz_long / S, (s + 1) nnz_long / S).  Short rows:
-    // a list of (row, CSR begin, degree).
-    const int32_t *lrow;     // [n_long] long rows in increasing order
-    const int32_t *lbeg;     // [n_long + 1] sequence position of each long row's first entry
-    const int32_t *lcsr;     // [n_long] CSR position of each long row's first entry
-    const int4 *srows;       // [n_short] short rows: (row, CSR begin, degree, 0)
-    const int32_t *k0;       // [S] long row holding the first entry of each range
-    uint32_t *counter;       // [S] pieces finished of the split row that starts in range s (zero between launches)
-    float *spart;            // [2 S][stride] partial sums: 2s = the row continued from before range s, 2s + 1 = the row continuing after it
-    int32_t n_long;
-    int32_t n_short;
-    int32_t S;
-    int32_t nnz_long;
 };
 
 __device__ __forceinline__ int graph_of(const int64_t *voff, int G, int64_t row) {
@@ -167,12 +150,152 @@ __global__ void k_init(const int64_t *__restrict__ rp, int64_t n, int32_t stride
 // ----------------------------------------------------------------------------
 // Helpers for the lane-group kernels
 // ----------------------------------------------------------------------------
+// Two FP32 additions (or fused multiply-adds) in one packed instruction; each
+// half is rounded as the scalar operation would be, so sums are unchanged.
+__device__ __forceinline__ void add_f32x2(float &a0, float &a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%0, %1};\n\tmov.b64 y, {%2, %3};\n\t"
+        "add.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;\n\t}"
+        : "+f"(a0), "+f"(a1) : "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fma_f32x2(float &a0, float &a1, float w, float b0, float b1) {
+    asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%0, %1};\n\tmov.b64 y, {%2, %3};\n\tmov.b64 z, {%4, %4};\n\t"
+        "fma.rn.f32x2 x, z, y, x;\n\tmov.b64 {%0, %1}, x;\n\t}"
+        : "+f"(a0), "+f"(a1) : "f"(b0), "f"(b1), "f"(w));
+}
+// acc[e] += f[e] (W: acc[e] = fmaf(w, f[e], acc[e])) for an even count of values
+template <int N, bool W>
+__device__ __forceinline__ void accumulate(float *acc, const float *f, float w) {
+#pragma unroll
+    for (int e = 0; e < N; e += 2) {
+        if (W) fma_f32x2(acc[e], acc[e + 1], w, f[e], f[e + 1]);
+        else add_f32x2(acc[e], acc[e + 1], f[e], f[e + 1]);
+    }
+}
 template <typename T, int LPR, int CPL>
 struct Lane {
     static constexpr int V = Store<T>::V;
     static constexpr int E = CPL * V;       // elements held by one lane
     static constexpr int G = 32 / LPR;      // groups per warp
 };
+
+// Gather-accumulate rows col[p] for p in [p0, p1) with the whole warp: group
+// grp takes every G-th neighbour.  Column indices (and weights) are read 32 at
+// a time, coalesced, and broadcast with shuffles; the next 32 are loaded
+// before the current ones are used, so their latency overlaps the row loads.
+// Each lane issues up to UB independent 16-byte row loads before it consumes
+// any of them, so that enough requests are in flight to cover the L2 latency.
+// W: edge weights present; without them no weight is read or broadcast and
+// the rows are plainly added (the same sums as fmaf with weight 1).
+template <typename T, int LPR, int CPL, bool W>
+__device__ __forceinline__ void warp_gather_w(const SweepArgs &a, int64_t p0, int64_t p1, int lane, int grp,
+                                              int gl, float (&acc)[CPL * Store<T>::V]) {
+    using L = Lane<T, LPR, CPL>;
+    constexpr int V = L::V, G = L::G;
+    constexpr int U = 32 / G;                       // neighbours per group per batch of 32
+    constexpr int UBc = AD_SWEEP_UB / CPL > 0 ? AD_SWEEP_UB / CPL : 1;
+    constexpr int UB = UBc < U ? UBc : U;          // loads in flight per chunk slot
+    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
+    const int64_t row_q = a.stride / V;   // 16-byte chunks per row
+    int32_t cjn = 0;
+    float wjn = 0.f;
+    if (p0 + lane < p1) {
+        cjn = ld_stream(a.col + p0 + lane);
+        if (W) wjn = ld_stream(a.w + p0 + lane);
+    }
+    for (int64_t base = p0; base < p1; base += 32) {
+        const int32_t cj = cjn;
+        const float wj = wjn;
+        const int64_t pn = base + 32 + lane;
+        if (pn < p1) {
+            cjn = ld_stream(a.col + pn);
+            if (W) wjn = ld_stream(a.w + pn);
+        }
+        const int cnt = (int)(p1 - base < 32 ? p1 - base : 32);
+#pragma unroll
+        for (int u0 = 0; u0 < U; u0 += UB) {
+            if (u0 * G >= cnt) break;
+            uint4 v[UB][CPL];
+            float wt[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int src = (u0 + u) * G + grp;
+                const int32_t nb = __shfl_sync(0xffffffffu, cj, src);
+                if (W) wt[u] = __shfl_sync(0xffffffffu, wj, src);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const int q = gl + c * LPR;
+                    v[u][c] = (src < cnt && q < a.nchunks) ? __ldg(X + (int64_t)nb * row_q + q) : make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u)
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    float f[V];
+                    Store<T>::unpack(v[u][c], f);
+                    accumulate<V, W>(acc + c * V, f, W ? wt[u] : 1.f);
+                }
+        }
+    }
+}
+
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int64_t p1, int lane, int grp,
+                                            int gl, float (&acc)[CPL * Store<T>::V]) {
+    if (!a.w) {   // the weighted loop reads a.w: it is reached only with weights present
+        warp_gather_w<T, LPR, CPL, false>(a, p0, p1, lane, grp, gl, acc);
+        return;
+    }
+    warp_gather_w<T, LPR, CPL, true>(a, p0, p1, lane, grp, gl, acc);
+}
+
+// Gather-accumulate a short row (<= kSmallUnroll entries per round) with one
+// lane group: all of its column indices, then all row loads, then the sums.
+constexpr int kSmallUnroll = AD_SWEEP_UB;
+template <typename T, int LPR, int CPL, bool W>
+__device__ __forceinline__ void group_gather_w(const SweepArgs &a, int64_t p0, int64_t p1, int gl,
+                                               float (&acc)[CPL * Store<T>::V]) {
+    constexpr int V = Store<T>::V;
+    constexpr int UB = (kSmallUnroll / CPL) > 0 ? (kSmallUnroll / CPL) : 1;
+    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
+    const int64_t row_q = a.stride / V;
+    for (int64_t base = p0; base < p1; base += UB) {
+        int32_t nb[UB];
+        float wt[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const bool ok = base + u < p1;
+            nb[u] = ok ? ld_stream(a.col + base + u) : 0;
+            if (W) wt[u] = ok ? ld_stream(a.w + base + u) : 0.f;
+        }
+        uint4 v[UB][CPL];
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                const int q = gl + c * LPR;
+                v[u][c] = (base + u < p1 && q < a.nchunks) ? __ldg(X + (int64_t)nb[u] * row_q + q) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                float f[V];
+                Store<T>::unpack(v[u][c], f);
+                accumulate<V, W>(acc + c * V, f, W ? wt[u] : 1.f);
+            }
+    }
+}
+
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void group_gather(const SweepArgs &a, int64_t p0, int64_t p1, int gl,
+                                             float (&acc)[CPL * Store<T>::V]) {
+    if (!a.w) {   // the weighted loop reads a.w: it is reached only with weights present
+        group_gather_w<T, LPR, CPL, false>(a, p0, p1, gl, acc);
+        return;
+    }
+    group_gather_w<T, LPR, CPL, true>(a, p0, p1, gl, acc);
+}
 
 // Sum over the G groups of a warp (butterfly: every group ends with the total).
 template <int LPR, int E>
@@ -192,6 +315,40 @@ __device__ __forceinline__ void load_own(const SweepArgs &a, int64_t row, int gl
     for (int c = 0; c < CPL; ++c) {
         const int q = gl + c * LPR;
         own[c] = q < a.nchunks ? __ldg(X + row * row_q + q) : make_uint4(0, 0, 0, 0);
+    }
+}
+
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, int gl, const uint4 (&own)[CPL],
+                                             const float (&S)[CPL * Store<T>::V], const float *acg,
+                                             float (&mn)[CPL * Store<T>::V], float (&mx)[CPL * Store<T>::V]) {
+    constexpr int V = Store<T>::V;
+    uint4 *Y = reinterpret_cast<uint4 *>(a.x_out);
+    const int64_t row_q = a.stride / V;
+    const float dinv = __ldg(a.Dinv + row);
+    const float om = a.omega, om1 = 1.f - a.omega;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        const int q = gl + c * LPR;
+        if (q < a.nchunks) {
+            float y[V], o[V], A[V], C[V];
+            Store<T>::unpack(own[c], y);
+#pragma unroll
+            for (int e4 = 0; e4 < V / 4; ++e4) {   // scale and centre of the row's graph (the same line for every row)
+                const float4 av = __ldg(reinterpret_cast<const float4 *>(acg + q * V) + e4);
+                const float4 cv = __ldg(reinterpret_cast<const float4 *>(acg + a.stride + q * V) + e4);
+                A[4 * e4] = av.x; A[4 * e4 + 1] = av.y; A[4 * e4 + 2] = av.z; A[4 * e4 + 3] = av.w;
+                C[4 * e4] = cv.x; C[4 * e4 + 1] = cv.y; C[4 * e4 + 2] = cv.z; C[4 * e4 + 3] = cv.w;
+            }
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const float z = fmaf(om1, y[e], om * (S[c * V + e] * dinv));
+                o[e] = Store<T>::round(A[e] * (z - C[e]));
+                mn[c * V + e] = fminf(mn[c * V + e], o[e]);
+                mx[c * V + e] = fmaxf(mx[c * V + e], o[e]);
+            }
+            Y[row * row_q + q] = Store<T>::pack(o);
+        }
     }
 }
 
@@ -280,366 +437,127 @@ struct LaneStats {
     }
 };
 
-template <typename T>
-constexpr int stream_minb() { return AD_STREAM_MINB; }
-
 // ----------------------------------------------------------------------------
-// Streaming JOR sweep (Alg. 1 inner loop), two phases in one launch.
-//
-// Long rows (degree > kShortMax).  Their entries, row after row, form one
-// sequence; it is cut into S ranges of equal length and lane group s walks
-// range s, U entries per batch: the column indices (and weights) of the next
-// batch are loaded while the current batch's U neighbour rows are in flight,
-// so every group keeps U row loads outstanding.  A long row has more entries
-// than a batch, so a batch holds at most one row change: entries before it
-// add to the finishing row, the rest to the next one, and the finishing row is
-// written after the batch.  A row that lies inside one range is summed by its
-// group in CSR order; a row cut by range ends ("split") leaves one partial sum
-// per range it touches, and the last piece to finish adds them in range order
-// and writes the row, so the result does not depend on timing.
-//
-// Short rows (degree 1 .. kShortMax).  One lane group per row, the row's
-// column indices in one load, all of its neighbour rows in flight at once, the
-// sum in CSR order; the groups of a warp take consecutive rows of the list and
-// warps stride over it.
-//
-// The groups of a warp run in lock step (every shuffle sees all lanes); row
-// changes are handled in a branch that the whole warp enters when any of its
-// groups needs it.
+// One JOR sweep (Alg. 1 inner loop) over all rows of degree > 0.
 // ----------------------------------------------------------------------------
-constexpr int kShortMax = 8;   // rows of degree <= kShortMax take the short-row phase (>= every batch size U)
-
-__device__ __forceinline__ int32_t range_of(int64_t p, int32_t S, int32_t len) {
-    // largest s with floor(s len / S) <= p
-    return (int32_t)(((p + 1) * (int64_t)S + len - 1) / len - 1);
-}
-
-template <typename T, int LPR, int CPL, int U>
-struct StreamLane {
-    static constexpr int V = Store<T>::V, E = CPL * V, G = 32 / LPR;
-    static constexpr int CU = (U + LPR - 1) / LPR;            // column registers per lane per batch
-    static constexpr int CS = (kShortMax + LPR - 1) / LPR;    // ... per short row
-    static constexpr int MPL = LPR >= 8 ? 1 : 8 / LPR;        // row-metadata registers per lane per window
-    static constexpr int W = LPR * MPL;                       // rows per metadata window
-    static_assert(U <= kShortMax, "a batch must be shorter than every long row");
-};
-
-// lrow / lbeg / lcsr of long rows kb + gl + c LPR (past the end: no row, a position never reached)
-template <int LPR, int MPL>
-__device__ __forceinline__ void stream_window(const SweepArgs &a, int64_t kb, int gl, int32_t (&wr)[MPL],
-                                              int32_t (&wb)[MPL], int32_t (&wc)[MPL]) {
+// Sum of the partial rows of one high-degree row (its chunks t0 .. t0 +
+// nchunk - 1): group g adds partials g, g + G, ... in order, then the groups'
+// sums are added (once per high-degree row).
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void sum_partials(const SweepArgs &a, int64_t t0, int32_t nchunk, int grp, int gl, float (&S)[CPL * Store<T>::V]) {
+    constexpr int V = Store<T>::V, E = CPL * V, G = 32 / LPR;
 #pragma unroll
-    for (int c = 0; c < MPL; ++c) {
-        const int64_t k = kb + gl + c * LPR;
-        wr[c] = k < a.n_long ? __ldg(a.lrow + k) : 0;
-        wb[c] = k <= a.n_long ? __ldg(a.lbeg + k) : 0x7fffffff;
-        wc[c] = k < a.n_long ? __ldg(a.lcsr + k) : 0;
+    for (int e = 0; e < E; ++e) S[e] = 0.f;
+    for (int32_t cc2 = grp; cc2 < nchunk; cc2 += G) {
+        const float4 *pp = reinterpret_cast<const float4 *>(a.part + (t0 + cc2) * (int64_t)a.stride);
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+            const int q = gl + cc * LPR;
+            if (q < a.nchunks) {
+#pragma unroll
+                for (int e4 = 0; e4 < V / 4; ++e4) {
+                    const float4 f = __ldcg(pp + (q * V) / 4 + e4);
+                    S[cc * V + 4 * e4 + 0] += f.x;
+                    S[cc * V + 4 * e4 + 1] += f.y;
+                    S[cc * V + 4 * e4 + 2] += f.z;
+                    S[cc * V + 4 * e4 + 3] += f.w;
+                }
+            }
+        }
     }
+    reduce_groups<LPR, E>(S);
 }
 
-template <typename T, int LPR, int CPL, int U, bool WT, bool BATCH>
-__device__ __forceinline__ void sweep_stream_body(const SweepArgs &a, float *sm) {
-    using SL = StreamLane<T, LPR, CPL, U>;
-    constexpr int V = SL::V, E = SL::E, G = SL::G, CU = SL::CU, CS = SL::CS, MPL = SL::MPL, W = SL::W;
+// More warps per SM hide more of the gather latency even at the cost of a few
+// spilled registers: measured best at 6 CTAs (FP32) and 5 (16-bit) per SM.
+template <typename T>
+constexpr int sweep_minb() { return sizeof(T) == 4 ? AD_SWEEP_MINB : AD_SWEEP_MINB16; }
+
+template <typename T, int LPR, int CPL>
+__global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
+    using L = Lane<T, LPR, CPL>;
+    constexpr int V = L::V, E = L::E, G = L::G;
+    extern __shared__ float sm[];   // [2][warps][stride]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int grp = lane / LPR, gl = lane % LPR;
-    const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (grp * LPR));
-    const int32_t gwarp = (int32_t)((int64_t)blockIdx.x * nwarps + warp);
-    const int32_t gid = gwarp * G + grp;
-    const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
-    const int32_t row_q = a.stride / V;
 
     LaneStats<T, LPR, CPL> ls;
     ls.enter(a, gl, 0, false);
-    int32_t gbeg = 0, gend = 0;   // rows of graph ls.cg (batches only)
-    if (BATCH) gend = (int32_t)__ldg(a.voff + 1);
+    auto row_graph = [&](int64_t row) { return a.G > 1 ? graph_of(a.voff, a.G, row) : 0; };
 
-    // row r's output: z = (1-omega) s_r + omega Dinv_r S, stored as a (z - c), min/max tracked
-    auto epilogue = [&](int32_t r, const uint4 (&ow)[CPL], float di, const float (&S)[E]) {
-        if (BATCH && (r >= gend || r < gbeg)) {
-            ls.enter(a, gl, graph_of(a.voff, a.G, r), true);
-            gbeg = (int32_t)__ldg(a.voff + ls.cg);
-            gend = (int32_t)__ldg(a.voff + ls.cg + 1);
-        }
-        uint4 *Y = reinterpret_cast<uint4 *>(a.x_out);
-        const float om = a.omega, om1 = 1.f - a.omega;
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int q = gl + c * LPR;
-            if (q < a.nchunks) {
-                float y[V], o[V];
-                Store<T>::unpack(ow[c], y);
-#pragma unroll
-                for (int e4 = 0; e4 < V / 4; ++e4) {
-                    const float4 av = __ldg(reinterpret_cast<const float4 *>(ls.acg + q * V) + e4);
-                    const float4 cv = __ldg(reinterpret_cast<const float4 *>(ls.acg + a.stride + q * V) + e4);
-                    const float A[4] = {av.x, av.y, av.z, av.w}, C[4] = {cv.x, cv.y, cv.z, cv.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int e = 4 * e4 + i;
-                        const float z = fmaf(om1, y[e], om * (S[c * V + e] * di));
-                        o[e] = Store<T>::round(A[i] * (z - C[i]));
-                        ls.mn[c * V + e] = fminf(ls.mn[c * V + e], o[e]);
-                        ls.mx[c * V + e] = fmaxf(ls.mx[c * V + e], o[e]);
-                    }
-                }
-                Y[(int64_t)r * row_q + q] = Store<T>::pack(o);
-            }
-        }
-    };
-    auto add = [&](float (&dst)[E], const uint4 (&vu)[CPL], float w) {
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            float f[V];
-            Store<T>::unpack(vu[c], f);
-#pragma unroll
-            for (int e = 0; e < V; ++e) dst[c * V + e] = WT ? fmaf(w, f[e], dst[c * V + e]) : dst[c * V + e] + f[e];
-        }
-    };
-
-    // ======================= long rows =======================
-    if (a.n_long > 0) {
-        const bool has = gid < a.S;
-        const int32_t s0 = has ? (int32_t)((int64_t)gid * a.nnz_long / a.S) : 0;
-        const int32_t s1 = has ? (int32_t)(((int64_t)gid + 1) * a.nnz_long / a.S) : 0;
-        // k: current long row; row = lrow[k]; sequence [rs, re); CSR begins cs (row k), cn (k + 1), cn2 (k + 2);
-        // rn2 = end of row k + 1.  Rows kb .. kb + 2W - 1 are held in the window.
-        int64_t k = has ? __ldg(a.k0 + gid) : 0;
-        int64_t kb = k;
-        int32_t wr[MPL], wb[MPL], wc[MPL], nr[MPL], nb2[MPL], nc[MPL];
-        stream_window<LPR, MPL>(a, kb, gl, wr, wb, wc);
-        stream_window<LPR, MPL>(a, kb + W, gl, nr, nb2, nc);
-        auto fetch = [&](int64_t kk, int32_t &r_out, int32_t &b_out, int32_t &c_out) {
-            const int rel = (int)(kk - kb);
-            const int src = grp * LPR + rel % LPR, slot = (rel % W) / LPR;
-            const bool second = rel >= W;
-#pragma unroll
-            for (int c = 0; c < MPL; ++c) {
-                const int32_t tr = __shfl_sync(0xffffffffu, second ? nr[c] : wr[c], src);
-                const int32_t tb = __shfl_sync(0xffffffffu, second ? nb2[c] : wb[c], src);
-                const int32_t tc = __shfl_sync(0xffffffffu, second ? nc[c] : wc[c], src);
-                if (c == slot) { r_out = tr; b_out = tb; c_out = tc; }
-            }
-        };
-        int32_t row = 0, rs = 0, re = 0, rn2 = 0, cs = 0, cn = 0, cn2 = 0, tmp = 0;
-        fetch(k, row, rs, cs);
-        fetch(k + 1, tmp, re, cn);
-        fetch(k + 2, tmp, rn2, cn2);
-        if (!has) { re = 0x7fffffff; rn2 = 0x7fffffff; }
-
-        uint4 own[CPL];
-        float dinv = 0.f;
-        if (has) {
-            load_own<T, LPR, CPL>(a, row, gl, own);
-            dinv = __ldg(a.Dinv + row);
-        }
+    const int64_t W = (int64_t)gridDim.x * nwarps;
+    const TaskIter it = task_iter(a.n_tasks, (int64_t)blockIdx.x * nwarps + warp, W, a.blocked);
+    for (int64_t task = it.t; task < it.t_end; task += it.step) {
         float acc[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) acc[e] = 0.f;
-
-        // A split row whose last piece this group finished: combined after the batch.
-        int32_t pend_row = -1, pend_r0 = 0, pend_r1 = 0;
-        auto finish = [&]() {
-            if (rs >= s0 && re <= s1) {   // the whole row lies in this range
-                epilogue(row, own, dinv, acc);
-                return;
-            }
-            const int64_t slot = 2 * (int64_t)gid + (rs < s0 ? 0 : 1);
-            float *pp = a.spart + slot * a.stride;
+        if (task < a.n_big) {
+            // ---- a chunk of a high-degree row; the last chunk combines
+            const int64_t row = a.big_row[task];
+            const int32_t c = a.big_chunk[task];
+            const int64_t rb = a.rp[row], re = a.rp[row + 1];
+            const int64_t p0 = rb + (int64_t)c * kChunk, p1 = min(re, p0 + kChunk);
+            warp_gather<T, LPR, CPL>(a, p0, p1, lane, grp, gl, acc);
+            reduce_groups<LPR, E>(acc);
+            float *part = a.part + task * (int64_t)a.stride;
+            if (grp == 0) {
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) {
-                const int q = gl + c * LPR;
-                if (q < a.nchunks) {
+                for (int cc = 0; cc < CPL; ++cc) {
+                    const int q = gl + cc * LPR;
+                    if (q < a.nchunks) {
 #pragma unroll
-                    for (int e4 = 0; e4 < V / 4; ++e4)
-                        __stcg(reinterpret_cast<float4 *>(pp + q * V) + e4,
-                               make_float4(acc[c * V + 4 * e4], acc[c * V + 4 * e4 + 1], acc[c * V + 4 * e4 + 2],
-                                           acc[c * V + 4 * e4 + 3]));
+                        for (int e = 0; e < V; ++e) __stcg(part + q * V + e, acc[cc * V + e]);
+                    }
                 }
+                __threadfence();
             }
-            __threadfence();
-            __syncwarp(gmask);
-            const int32_t r0 = range_of(rs, a.S, a.nnz_long), r1 = range_of((int64_t)re - 1, a.S, a.nnz_long);
+            __syncwarp();
+            const int64_t t0 = task - c;
+            const int32_t nchunk = (int32_t)((re - rb + kChunk - 1) / kChunk);
             uint32_t old = 0;
-            if (gl == 0) old = atomicAdd(a.counter + r0, 1u);
-            old = __shfl_sync(gmask, old, grp * LPR);
-            if (old == (uint32_t)(r1 - r0)) { pend_row = row; pend_r0 = r0; pend_r1 = r1; }
-        };
-        // partials of a split row in range order (a few loads in flight), then its output
-        auto combine = [&]() {
-            __threadfence();
-            uint4 ow[CPL];
-            load_own<T, LPR, CPL>(a, pend_row, gl, ow);
-            const float di = __ldg(a.Dinv + pend_row);
-            float S[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) S[e] = 0.f;
-            constexpr int UC = 4;
-            for (int32_t rb = pend_r0; rb <= pend_r1; rb += UC) {
-                float4 f[UC][E / 4];
-#pragma unroll
-                for (int u = 0; u < UC; ++u) {
-                    const int32_t rr = rb + u;
-                    const int64_t sl = rr == pend_r0 ? 2 * (int64_t)rr + 1 : 2 * (int64_t)rr;
-#pragma unroll
-                    for (int c = 0; c < CPL; ++c) {
-                        const int q = gl + c * LPR;
-#pragma unroll
-                        for (int e4 = 0; e4 < V / 4; ++e4)
-                            f[u][c * (V / 4) + e4] = (rr <= pend_r1 && q < a.nchunks)
-                                ? __ldcg(reinterpret_cast<const float4 *>(a.spart + sl * a.stride + q * V) + e4)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < UC; ++u)
-#pragma unroll
-                    for (int i = 0; i < E / 4; ++i) {
-                        S[4 * i + 0] += f[u][i].x;
-                        S[4 * i + 1] += f[u][i].y;
-                        S[4 * i + 2] += f[u][i].z;
-                        S[4 * i + 3] += f[u][i].w;
-                    }
-            }
-            epilogue(pend_row, ow, di, S);
-            if (gl == 0) a.counter[pend_r0] = 0u;
-            pend_row = -1;
-        };
-        // the row change of the groups with `ends`, the next row's sum starting from carry
-        auto next_row = [&](bool ends, const float (&carry)[E]) {
-            if (ends) {
-                finish();
-                ++k;
-                if (k - kb == W) {   // into the second half of the window; load the one after it
-                    kb += W;
-#pragma unroll
-                    for (int c = 0; c < MPL; ++c) { wr[c] = nr[c]; wb[c] = nb2[c]; wc[c] = nc[c]; }
-                    stream_window<LPR, MPL>(a, kb + W, gl, nr, nb2, nc);
-                }
-            }
-            int32_t nrow = 0, b2 = 0, c2 = 0;
-            fetch(k, nrow, tmp, tmp);
-            fetch(k + 2, tmp, b2, c2);
-            if (ends) {
-                row = nrow;
-                rs = re; re = rn2; rn2 = b2;
-                cs = cn; cn = cn2; cn2 = c2;
+            if (lane == 0) old = atomicAdd(a.big_counter + t0, 1u);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old == (uint32_t)(nchunk - 1)) {
+                __threadfence();
+                // group g sums partials g, g + G, ... (fixed order); then the groups' sums are added
+                uint4 own[CPL];
                 load_own<T, LPR, CPL>(a, row, gl, own);
-                dinv = __ldg(a.Dinv + row);
-#pragma unroll
-                for (int e = 0; e < E; ++e) acc[e] = carry[e];
-            }
-        };
-        // CSR position of sequence position q (q in rows k .. k + 2)
-        auto csr_of = [&](int64_t q) -> int64_t {
-            return q < re ? cs + (q - rs) : (q < rn2 ? cn + (q - re) : cn2 + (q - rn2));
-        };
-        auto load_cols = [&](int64_t p, int32_t (&cj)[CU], float (&cw)[CU]) {
-#pragma unroll
-            for (int c = 0; c < CU; ++c) {
-                const int64_t q = p + gl + c * LPR;
-                const bool ok = gl + c * LPR < U && q < s1;
-                const int64_t pos = csr_of(q);
-                cj[c] = ok ? ld_stream(a.col + pos) : 0;
-                if (WT) cw[c] = ok ? ld_stream(a.w + pos) : 0.f;
-            }
-        };
-
-        const int32_t len = s1 - s0;
-        const int nbt = __reduce_max_sync(0xffffffffu, (len + U - 1) / U);
-        int32_t cj[CU], cjn[CU];
-        float cw[CU], cwn[CU];
-        load_cols(s0, cj, cw);
-        for (int b = 0; b < nbt; ++b) {
-            const int32_t p = s0 + b * U;
-            uint4 v[U][CPL];
-            float wt[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int src = grp * LPR + u % LPR;
-                const int32_t j = __shfl_sync(0xffffffffu, cj[u / LPR], src);
-                wt[u] = WT ? __shfl_sync(0xffffffffu, cw[u / LPR], src) : 1.f;
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                    const int q = gl + c * LPR;
-                    v[u][c] = (p + u < s1 && q < a.nchunks) ? __ldg(X + (int64_t)j * row_q + q)
-                                                            : make_uint4(0, 0, 0, 0);
+                float S[E];
+                sum_partials<T, LPR, CPL>(a, t0, nchunk, grp, gl, S);
+                if (grp == 0) {
+                    ls.enter(a, gl, row_graph(row), true);
+                    row_epilogue<T, LPR, CPL>(a, row, gl, own, S, ls.acg, ls.mn, ls.mx);
                 }
+                if (lane == 0) a.big_counter[t0] = 0u;
             }
-            load_cols(p + U, cjn, cwn);
-            const bool end_in = re < min(p + U, s1);   // the group's row ends inside the batch (at most once)
-            if (!__any_sync(0xffffffffu, end_in)) {
-#pragma unroll
-                for (int u = 0; u < U; ++u) add(acc, v[u], wt[u]);
-            } else {
-                float acc2[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) acc2[e] = 0.f;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (p + u < re) add(acc, v[u], wt[u]);
-                    else add(acc2, v[u], wt[u]);
-                }
-                next_row(end_in, acc2);
-                if (__any_sync(0xffffffffu, pend_row >= 0)) {
-                    if (pend_row >= 0) combine();
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CU; ++c) { cj[c] = cjn[c]; if (WT) cw[c] = cwn[c]; }
-        }
-        if (has && len > 0) finish();   // the row holding the range's last entry
-        if (pend_row >= 0) combine();
-    }
-
-    // ======================= short rows =======================
-    {
-        const int32_t total_warps = (int32_t)(gridDim.x * nwarps);
-        const int32_t n_tasks = (a.n_short + G - 1) / G;
-        for (int32_t t = gwarp; t < n_tasks; t += total_warps) {
-            const int32_t sk = t * G + grp;
-            const int4 sr = sk < a.n_short ? __ldg(a.srows + sk) : make_int4(0, 0, 0, 0);
-            const int32_t row = sr.x, beg = sr.y, deg = sr.z;
-            int32_t cj[CS];
-            float cw[CS];
-#pragma unroll
-            for (int c = 0; c < CS; ++c) {
-                const int u = gl + c * LPR;
-                const bool ok = u < deg;
-                cj[c] = ok ? ld_stream(a.col + beg + u) : 0;
-                if (WT) cw[c] = ok ? ld_stream(a.w + beg + u) : 0.f;
-            }
+        } else if (task < a.n_big + a.n_medium) {
+            // ---- one row, whole warp
+            const int64_t row = a.medium_row[task - a.n_big];
             uint4 own[CPL];
-            float dinv = 0.f;
-            if (deg > 0) {
+            load_own<T, LPR, CPL>(a, row, gl, own);
+            warp_gather<T, LPR, CPL>(a, a.rp[row], a.rp[row + 1], lane, grp, gl, acc);
+            reduce_groups<LPR, E>(acc);
+            if (grp == 0) {
+                ls.enter(a, gl, row_graph(row), true);
+                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.acg, ls.mn, ls.mx);
+            }
+        } else {
+            // ---- G low-degree rows, one per lane group
+            const int64_t si = (task - a.n_big - a.n_medium) * G + grp;
+            if (si < a.n_small_rows) {
+                const int64_t row = a.small_row[si];
+                uint4 own[CPL];
                 load_own<T, LPR, CPL>(a, row, gl, own);
-                dinv = __ldg(a.Dinv + row);
+                group_gather<T, LPR, CPL>(a, a.rp[row], a.rp[row + 1], gl, acc);
+                ls.enter(a, gl, row_graph(row), true);
+                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.acg, ls.mn, ls.mx);
             }
-            uint4 v[kShortMax][CPL];
-            float wt[kShortMax];
-#pragma unroll
-            for (int u = 0; u < kShortMax; ++u) {
-                const int src = grp * LPR + u % LPR;
-                const int32_t j = __shfl_sync(0xffffffffu, cj[u / LPR], src);
-                wt[u] = WT ? __shfl_sync(0xffffffffu, cw[u / LPR], src) : 1.f;
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                    const int q = gl + c * LPR;
-                    v[u][c] = (u < deg && q < a.nchunks) ? __ldg(X + (int64_t)j * row_q + q) : make_uint4(0, 0, 0, 0);
-                }
-            }
-            float acc[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] = 0.f;
-#pragma unroll
-            for (int u = 0; u < kShortMax; ++u)
-                if (u < deg) add(acc, v[u], wt[u]);
-            if (deg > 0) epilogue(row, own, dinv, acc);
         }
     }
 
     // ---- min/max of what this CTA stored -> atomics
-    if (BATCH) {
+    if (a.G > 1) {
+        // lanes of a warp that share one graph are reduced first
         const bool same = __all_sync(0xffffffffu, ls.cg == __shfl_sync(0xffffffffu, ls.cg, 0));
         if (same) {
 #pragma unroll
@@ -685,18 +603,6 @@ __device__ __forceinline__ void sweep_stream_body(const SweepArgs &a, float *sm)
             atomicMax(a.mm_max + r, f2ord(hi));
         }
     }
-}
-
-// row loads in flight per lane of the streaming sweep: 8 for FP32 rows, 4 for
-// 16-bit rows (whose lanes hold twice the values)
-template <typename T>
-constexpr int stream_u() { return sizeof(T) == 4 ? AD_STREAM_U32 : AD_STREAM_U16; }
-
-template <typename T, int LPR, int CPL, bool BATCH>
-__global__ void __launch_bounds__(256, stream_minb<T>()) k_sweep_stream(SweepArgs a) {
-    extern __shared__ float sm[];   // [2][warps][stride]
-    if (a.w) sweep_stream_body<T, LPR, CPL, stream_u<T>() / CPL, true, BATCH>(a, sm);
-    else sweep_stream_body<T, LPR, CPL, stream_u<T>() / CPL, false, BATCH>(a, sm);
 }
 
 // ----------------------------------------------------------------------------
@@ -859,47 +765,11 @@ struct Config {
 };
 
 
-// One streaming sweep: ranges sized so that every resident lane group of the
-// launch walks one range (fewer, of >= 32 entries each, on small graphs).
 template <typename T, int LPR, int CPL>
-ad_status launch_sweep_stream(ad_graph_t g, const SweepArgs &a, int per_sm_cap, size_t smem) {
-    if (g->nnz > (int64_t)0x7fffffff - 256)   // positions and batch ends are 32-bit in the kernel
-        return fail(AD_ERR_INVALID_ARG, "too many CSR entries for the streaming sweep");
-    const bool batch = a.G > 1;
-    int per_sm = 0;
-    if (batch) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_stream<T, LPR, CPL, true>, 256, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_stream<T, LPR, CPL, false>, 256, smem);
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm_cap > 0 && per_sm_cap < per_sm) per_sm = per_sm_cap;
-    const int64_t groups_per_block = 8 * (32 / LPR);
-    int64_t S = (int64_t)per_sm * g->num_sms * groups_per_block;
-
-    StreamPlan *sp = nullptr;
-    AD_TRY(get_stream_plan(g, (int32_t)S, &sp));
-    S = sp->S;
-    AD_TRY(ensure(g, g->part, (size_t)2 * S * a.stride * sizeof(float)));
-    SweepArgs b = a;
-    b.lrow = g->lrow;
-    b.lbeg = g->lbeg;
-    b.lcsr = g->lcsr;
-    b.srows = reinterpret_cast<const int4 *>(g->srows);
-    b.k0 = sp->k0;
-    b.counter = sp->counter;
-    b.spart = static_cast<float *>(g->part.ptr);
-    b.n_long = (int32_t)g->n_long;
-    b.n_short = (int32_t)g->n_short;
-    b.S = (int32_t)S;
-    b.nnz_long = (int32_t)g->nnz_long;
-    // every resident group walks one range (fewer ranges, of >= 32 entries, on small graphs),
-    // and up to one group per short row
-    int64_t need = std::max<int64_t>(S, g->n_short);
-    const int64_t cap = (int64_t)per_sm * g->num_sms * groups_per_block;
-    if (need > cap) need = cap;
-    const int blocks = (int)std::max<int64_t>(1, (need + groups_per_block - 1) / groups_per_block);
+ad_status launch_sweep(ad_graph_t g, const SweepArgs &a, int blocks, size_t smem) {
     AD_LAUNCH(k_scale_center<T>, a.G, 32, 0, g->stream, a.mm_prev_min, a.mm_prev_max, a.x_in, a.anchor, a.stride,
               a.ac);
-    if (batch) AD_LAUNCH((k_sweep_stream<T, LPR, CPL, true>), blocks, 256, smem, g->stream, b);
-    else AD_LAUNCH((k_sweep_stream<T, LPR, CPL, false>), blocks, 256, smem, g->stream, b);
+    AD_LAUNCH((k_sweep<T, LPR, CPL>), blocks, 256, smem, g->stream, a);
     return AD_OK;
 }
 template <typename T, int LPR, int CPL>
@@ -908,9 +778,12 @@ ad_status launch_distance(ad_graph_t g, const SweepArgs &a, int blocks) {
     return AD_OK;
 }
 template <typename T, int LPR, int CPL>
-int distance_blocks_per_sm() {
+int blocks_for(bool sweep, size_t smem) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_distance<T, LPR, CPL>, 256, 0);
+    if (sweep)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T, LPR, CPL>, 256, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_distance<T, LPR, CPL>, 256, 0);
     return per_sm > 0 ? per_sm : 1;
 }
 
@@ -920,11 +793,13 @@ ad_status dispatch(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &
     // persistent grid: every SM full, but no more warps than tasks
     auto run = [&](auto lpr_c, auto cpl_c) -> ad_status {
         constexpr int LPR = decltype(lpr_c)::value, CPL = decltype(cpl_c)::value;
-        if (sweep) return launch_sweep_stream<T, LPR, CPL>(g, a, cf.per_sm, smem);
-        int64_t blocks = (int64_t)distance_blocks_per_sm<T, LPR, CPL>() * g->num_sms;
+        int per_sm = blocks_for<T, LPR, CPL>(sweep, smem);
+        if (sweep && cf.per_sm > 0 && cf.per_sm < per_sm) per_sm = cf.per_sm;
+        int64_t blocks = (int64_t)per_sm * g->num_sms;
         const int64_t need = (n_tasks + 7) / 8;
         if (blocks > need) blocks = need > 0 ? need : 1;
-        return launch_distance<T, LPR, CPL>(g, a, (int)blocks);
+        return sweep ? launch_sweep<T, LPR, CPL>(g, a, (int)blocks, smem)
+                     : launch_distance<T, LPR, CPL>(g, a, (int)blocks);
     };
     using std::integral_constant;
     switch (cf.lpr * 100 + cf.cpl) {
@@ -935,6 +810,12 @@ ad_status dispatch(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &
         case 1601: return run(integral_constant<int, 16>{}, integral_constant<int, 1>{});
         case 3201: return run(integral_constant<int, 32>{}, integral_constant<int, 1>{});
         case 3202: return run(integral_constant<int, 32>{}, integral_constant<int, 2>{});
+        // fewer lanes per row, more chunks per lane: the alternative shapes the autotuner tries
+        case 102: return run(integral_constant<int, 1>{}, integral_constant<int, 2>{});
+        case 202: return run(integral_constant<int, 2>{}, integral_constant<int, 2>{});
+        case 402: return run(integral_constant<int, 4>{}, integral_constant<int, 2>{});
+        case 802: return run(integral_constant<int, 8>{}, integral_constant<int, 2>{});
+        case 1602: return run(integral_constant<int, 16>{}, integral_constant<int, 2>{});
         default: return fail(AD_ERR_INVALID_ARG, "unsupported R / storage combination");
     }
 }
