@@ -88,6 +88,7 @@ typedef enum {
 /* ad_algebraic_distance flags */
 #define AD_DIST_NORMALIZE 0x1           /* score rho * sqrt(D_i D_j): the optional last line of Alg. 1 */
 #define AD_DIST_KEEP_STATE 0x2          /* keep sqrt(k) checkpoints for ad_algebraic_distance_backward */
+#define AD_DIST_PERSISTENT 0x4          /* init, all sweeps and distances in one persistent launch (single graphs) */
 
 typedef struct ad_graph_s *ad_graph_t;
 typedef struct ad_ml_s *ad_ml_t;
@@ -134,6 +135,17 @@ ad_status ad_graph_set_profiling(ad_graph_t g, int32_t enable);
  * reset != 0 clears the counters after reading.
  */
 ad_status ad_graph_phase_time(ad_graph_t g, const char *phase, double *total_ms, int64_t *launches, int32_t reset);
+
+/*
+ * Self-test of the bounded grid-wide wait used by the persistent relaxation:
+ * a cooperative launch of two CTAs on stream whose barrier waits for an
+ * arrival that never comes, polling at most `polls` times.  *status_out
+ * receives the status the waiting kernel recorded (AD_ERR_TIMEOUT when the
+ * limit works); the context stays usable.  The paper has no counterpart: this
+ * checks the failure path of the library itself.  Errors: AD_ERR_INVALID_ARG,
+ * AD_ERR_CUDA, AD_ERR_STATE (a CTA passed the barrier).
+ */
+ad_status ad_selftest_barrier_timeout(void *stream, uint32_t polls, int32_t *status_out);
 
 /* ------------------------------------------------------------------------ */
 /* Graphs                                                                    */
@@ -214,7 +226,14 @@ ad_status ad_graph_set_edge_weights(ad_graph_t g, const float *w_edge);
  * accumulation either way).  rho_out[m] may be NULL; the scores are kept in
  * the handle for ad_sparsify either way.  With AD_DIST_KEEP_STATE the
  * iterates needed by ad_algebraic_distance_backward are kept (ceil(sqrt k)
- * checkpoints).  Errors: AD_ERR_INVALID_ARG, AD_ERR_OOM, AD_ERR_CUDA.
+ * checkpoints).  With AD_DIST_PERSISTENT a single graph (not a batch) is
+ * computed in one persistent cooperative launch: init, the k sweeps separated
+ * by grid-wide barriers (each rescale needs the min/max over all vertices),
+ * then the distances, with bit-identical results; a barrier waits at most a
+ * few seconds and then ends the launch with AD_ERR_TIMEOUT (reported by calls
+ * made outside a stream capture).  The multilevel functions relax every
+ * level this way.
+ * Errors: AD_ERR_INVALID_ARG, AD_ERR_OOM, AD_ERR_CUDA, AD_ERR_TIMEOUT.
  */
 ad_status ad_algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, uint64_t seed,
                                 uint32_t stream_id, ad_storage storage, int32_t flags, float *rho_out);

@@ -27,6 +27,7 @@ AD_STORAGE_FP32, AD_STORAGE_BF16, AD_STORAGE_FP16, AD_STORAGE_Q16 = 0, 1, 2, 3
 AD_CREATE_SKIP_VALIDATION = 0x1
 AD_DIST_NORMALIZE = 0x1
 AD_DIST_KEEP_STATE = 0x2
+AD_DIST_PERSISTENT = 0x4
 
 MODES = {"local": AD_MODE_LOCAL, "global": AD_MODE_GLOBAL}
 SCOPES = {"per_node": AD_SCOPE_PER_NODE, "whole_graph": AD_SCOPE_WHOLE_GRAPH}
@@ -57,6 +58,7 @@ _SIGS = {
     "ad_last_error": (ctypes.c_char_p, []),
     "ad_set_allocator": (ctypes.c_int, [_VP, _VP, _VP]),
     "ad_kernel_launch_count": (_U64, []),
+    "ad_selftest_barrier_timeout": (ctypes.c_int, [_VP, _U32, _PI32]),
     "ad_graph_set_profiling": (ctypes.c_int, [_VP, _I32]),
     "ad_graph_phase_time": (ctypes.c_int, [_VP, ctypes.c_char_p, _PD, _PI64, _I32]),
     "ad_graph_create": (ctypes.c_int, [_I64, _VP, _VP, _VP, _I32, _VP, ctypes.POINTER(_VP)]),
@@ -154,6 +156,13 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)
+
+
+def ad_selftest_barrier_timeout(polls=1000, stream=None) -> int:
+    """Status recorded by a grid barrier that cannot complete (AD_ERR_TIMEOUT = 8 when the limit works)."""
+    st = ctypes.c_int32()
+    _check(load().ad_selftest_barrier_timeout(_stream_ptr(stream), int(polls), ctypes.byref(st)))
+    return st.value
 
 
 # --------------------------------------------------------------------------- allocator

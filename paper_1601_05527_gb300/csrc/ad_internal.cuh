@@ -53,6 +53,14 @@ extern std::atomic<uint64_t> g_launches;
 namespace ad {
 
 constexpr int kNumSMs = 152;  // GB300; the runtime value is queried, this is a default
+// single graphs with at most this many CSR entries are relaxed in one persistent launch
+// without being asked (AD_DIST_PERSISTENT).  Measured on GB300, per-sweep launches
+// replayed as a CUDA graph are faster for every size tried (the persistent kernel
+// must read the vectors past L1), so none are by default.
+#ifndef AD_PERSIST_MAX_NNZ
+#define AD_PERSIST_MAX_NNZ 0
+#endif
+constexpr int64_t kPersistMaxNnz = AD_PERSIST_MAX_NNZ;
 
 // ----------------------------------------------------------------------------
 // Device helpers
@@ -274,7 +282,7 @@ struct ad_graph_s {
     uint64_t rho_version = 0;    // bumped whenever rho is recomputed
 
     // cached scratch
-    ad::DevBuf x0, x1, part, mm, ws, ac;
+    ad::DevBuf x0, x1, part, mm, ws, ac, relax_sync;
 
     // profiling
     bool profiling = false;
@@ -369,6 +377,7 @@ ad_status select_per_node_at(ad_graph_t g, const float *score_dev, double e, ad_
 ad_status select_per_node_fit_ranked(ad_graph_t g, const uint32_t *rank_dev, double fraction, uint8_t *keep_dev,
                                      int64_t *n_kept, double *e_used);
 ad_status select_local_degree(ad_graph_t g, double fraction, uint8_t *keep_dev, int64_t *n_kept, double *e_used);
+ad_status row_ranks(ad_graph_t g, const uint32_t *ekey, uint32_t *rank_out, uint32_t *desc_scratch);
 
 // SparsifyB order (binned.cu)
 ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev,

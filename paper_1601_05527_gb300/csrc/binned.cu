@@ -177,10 +177,178 @@ __global__ void k_bin_ranks(const uint64_t *keys, const int64_t *vals, const int
     }
 }
 
+// ----------------------------------------------------------------------------
+// The same order from per-row ranks of 32-bit keys (rows of at most 2^18
+// entries, whose bins are then fewer than 2^14).  The round-robin rank of an
+// entry is its position when the row's entries are ordered by (its index
+// inside its bin, its bin's place in the random bin order): round r lists the
+// r-th entries of the bins, bins in their order.  So:
+//   1. rank by Philox word inside the row (ties by position);
+//   2. rank by (bin, that rank): the row in bin order, random order inside bins;
+//   3. the index r of each entry inside its bin, from the runs of equal bins;
+//   4. the bins of each row ordered by their Philox word (a sort of the runs);
+//   5. rank by (r, the bin's place) = the selection rank.
+// ----------------------------------------------------------------------------
+constexpr int kRowRankBits = 18;   // rank inside a row < 2^18
+constexpr int kBinOrderBits = 14;  // bins of a row < 2^14
+
+__global__ void k_bin_words(const int32_t *erow, const int64_t *eid, const float *xs, const float *lo, const double *h,
+                            int64_t nnz, uint64_t seed, uint32_t *bin, uint32_t *word, unsigned long long *max_bin) {
+    unsigned long long mb = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = erow[p];
+        const double hi_ = h[i];
+        int64_t b = 0;
+        if (hi_ > 0.0) b = (int64_t)floor(__ddiv_rn(__dsub_rn((double)xs[p], (double)lo[i]), hi_));
+        bin[p] = (uint32_t)b;
+        mb = (unsigned long long)b > mb ? (unsigned long long)b : mb;
+        word[p] = bin_word(seed, (uint64_t)eid[p], 0u);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = y > mb ? y : mb;
+    }
+    if ((threadIdx.x & 31) == 0 && mb) atomicMax(max_bin, mb);
+}
+
+__global__ void k_bin_key2(const uint32_t *bin, const uint32_t *rw, int64_t nnz, uint32_t *key) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        key[p] = (bin[p] << kRowRankBits) | rw[p];
+}
+
+// entries in (bin, word) order inside their rows: slot rp[row] + rank
+__global__ void k_bin_place(const int32_t *erow, const int64_t *rp, const uint32_t *s2, const uint32_t *bin, int64_t nnz,
+                            int32_t *sorted, uint32_t *sbin) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = rp[erow[p]] + s2[p];
+        sorted[slot] = (int32_t)p;
+        sbin[slot] = bin[p];
+    }
+}
+
+// slot s starts a run (a non-empty bin of a row) when its row or bin differs from slot s - 1
+__global__ void k_bin_run_starts(const int32_t *sorted, const int32_t *erow, const uint32_t *sbin, int64_t nnz,
+                                 int64_t *flag) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x)
+        flag[s] = (s == 0 || erow[sorted[s]] != erow[sorted[s - 1]] || sbin[s] != sbin[s - 1]) ? 1 : 0;
+}
+
+// per run: first slot, sort key (row, Philox word of the bin), run id; first run of each row
+__global__ void k_bin_run_keys(const int32_t *sorted, const int32_t *erow, const uint32_t *sbin, const int64_t *flag,
+                               const int64_t *run_of, int64_t nnz, uint64_t seed, int64_t *run_start, uint64_t *rkey,
+                               int64_t *rval, int64_t *row_runs) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[s]) continue;
+        const int64_t r = run_of[s];
+        const int32_t row = erow[sorted[s]];
+        run_start[r] = s;
+        rkey[r] = ((uint64_t)(uint32_t)row << 32) | bin_word(seed, (uint64_t)row, 1u + sbin[s]);
+        rval[r] = r;
+        if (s == 0 || erow[sorted[s - 1]] != row) row_runs[row] = r;
+    }
+}
+
+// place of each bin in its row's random bin order (rows keep their run ranges in the sorted order)
+__global__ void k_bin_order(const uint64_t *rkey, const int64_t *rval, const int64_t *row_runs, int64_t nruns,
+                            uint32_t *order) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nruns; j += (int64_t)gridDim.x * blockDim.x)
+        order[rval[j]] = (uint32_t)(j - row_runs[rkey[j] >> 32]);
+}
+
+// key of the round robin: (index inside the bin, place of the bin)
+__global__ void k_bin_key3(const int32_t *sorted, const int64_t *run_of, const int64_t *run_start, const uint32_t *order,
+                           int64_t nnz, uint32_t *key) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = run_of[s];
+        key[sorted[s]] = ((uint32_t)(s - run_start[r]) << kBinOrderBits) | order[r];
+    }
+}
+
+static ad_status binned_ranks_sorted(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev,
+                                     uint32_t *bin_dev);
+
 // Selection rank of every CSR entry under SparsifyB, written to rank_dev[nnz]
 // (device); bin_dev[nnz] (device, may be NULL) receives the bin of every entry.
 // score_dev: FP32 distances per edge (device).
 ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev, uint32_t *bin_dev) {
+    const int64_t n = g->n, nnz = g->nnz;
+    if (nnz == 0) return AD_OK;
+    AD_TRY(ensure_mirror(g));
+    AD_TRY(ensure_degree_classes(g));
+    const int64_t maxd = g->distinct_degrees.empty() ? 0 : g->distinct_degrees.back();
+    if (maxd >= ((int64_t)1 << kRowRankBits) || n >= ((int64_t)1 << 31))
+        return binned_ranks_sorted(g, score_dev, seed, rank_dev, bin_dev);
+    std::vector<double> cb(std::max<int32_t>(g->n_deg_classes, 1));
+    for (int32_t q = 0; q < g->n_deg_classes; ++q) cb[q] = std::cbrt((double)g->distinct_degrees[q]);
+    double *cbrt_dc = nullptr, *h = nullptr;
+    float *lo = nullptr, *xs = nullptr;
+    uint32_t *bin = nullptr, *key = nullptr, *rk = nullptr, *desc = nullptr, *sbin = nullptr, *order = nullptr;
+    int32_t *sorted = nullptr;
+    int64_t *flag = nullptr, *run_of = nullptr, *run_start = nullptr, *rval = nullptr, *row_runs = nullptr;
+    uint64_t *rkey = nullptr;
+    unsigned long long *max_bin = nullptr;
+    AD_TRY(dalloc_t(g, cb.size(), &cbrt_dc));
+    AD_TRY(dalloc_t(g, n + 1, &lo));
+    AD_TRY(dalloc_t(g, n + 1, &h));
+    AD_TRY(dalloc_t(g, nnz, &xs));
+    AD_TRY(dalloc_t(g, nnz, &bin));
+    AD_TRY(dalloc_t(g, nnz, &key));
+    AD_TRY(dalloc_t(g, nnz, &rk));
+    AD_TRY(dalloc_t(g, nnz, &desc));
+    AD_TRY(dalloc_t(g, 1, &max_bin));
+    AD_TRY(copy_in(g, cbrt_dc, cb.data(), cb.size() * sizeof(double)));
+    AD_CUDA_TRY(cudaMemsetAsync(max_bin, 0, sizeof(unsigned long long), g->stream));
+    const int big = g->num_sms * 16;
+    AD_LAUNCH(k_bin_gather, big, 256, 0, g->stream, g->eid, score_dev, nnz, xs);
+    AD_LAUNCH(k_bin_stats, (int)std::min<int64_t>((n + 7) / 8, big), 256, 0, g->stream, g->rp, xs, g->deg_class,
+              cbrt_dc, n, lo, h);
+    AD_LAUNCH(k_bin_words, big, 256, 0, g->stream, g->erow, g->eid, xs, lo, h, nnz, seed, bin, key, max_bin);
+    unsigned long long mb = 0;
+    AD_TRY(copy_out(g, &mb, max_bin, sizeof(mb)));
+    auto release = [&]() {
+        for (void *p : {(void *)cbrt_dc, (void *)lo, (void *)h, (void *)xs, (void *)bin, (void *)key, (void *)rk,
+                        (void *)desc, (void *)max_bin, (void *)sbin, (void *)sorted, (void *)flag, (void *)run_of,
+                        (void *)run_start, (void *)rval, (void *)row_runs, (void *)rkey, (void *)order})
+            if (p) dfree(g, p);
+    };
+    if (mb >= ((unsigned long long)1 << kBinOrderBits)) {   // (cannot happen below 2^18 entries per row)
+        release();
+        return binned_ranks_sorted(g, score_dev, seed, rank_dev, bin_dev);
+    }
+    if (bin_dev) AD_CUDA_TRY(cudaMemcpyAsync(bin_dev, bin, nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, g->stream));
+    AD_TRY(row_ranks(g, key, rk, desc));                                   // 1. by word
+    AD_LAUNCH(k_bin_key2, big, 256, 0, g->stream, bin, rk, nnz, key);
+    AD_TRY(row_ranks(g, key, rk, desc));                                   // 2. by (bin, word)
+    AD_TRY(dalloc_t(g, nnz, &sorted));
+    AD_TRY(dalloc_t(g, nnz, &sbin));
+    AD_TRY(dalloc_t(g, nnz, &flag));
+    AD_TRY(dalloc_t(g, nnz, &run_of));
+    AD_LAUNCH(k_bin_place, big, 256, 0, g->stream, g->erow, g->rp, rk, bin, nnz, sorted, sbin);
+    AD_LAUNCH(k_bin_run_starts, big, 256, 0, g->stream, sorted, g->erow, sbin, nnz, flag);
+    int64_t nruns = 0;
+    AD_TRY(exclusive_scan_i64(g, flag, run_of, nnz, &nruns));
+    AD_LAUNCH(k_bin_inclusive, big, 256, 0, g->stream, flag, nnz, run_of);  // 3. run of every slot
+    AD_TRY(dalloc_t(g, nruns + 1, &run_start));
+    AD_TRY(dalloc_t(g, nruns + 1, &rkey));
+    AD_TRY(dalloc_t(g, nruns + 1, &rval));
+    AD_TRY(dalloc_t(g, nruns + 1, &order));
+    AD_TRY(dalloc_t(g, n + 1, &row_runs));
+    AD_LAUNCH(k_bin_run_keys, big, 256, 0, g->stream, sorted, g->erow, sbin, flag, run_of, nnz, seed, run_start, rkey,
+              rval, row_runs);
+    std::vector<int> shifts = {0, 8, 16, 24};                              // 4. bins by word inside each row
+    for (int sh = 32; sh < 64 && ((uint64_t)(n - 1) >> (sh - 32)) != 0; sh += 8) shifts.push_back(sh);
+    AD_TRY(radix_sort_pairs(g, rkey, rval, nruns, shifts));
+    AD_LAUNCH(k_bin_order, big, 256, 0, g->stream, rkey, rval, row_runs, nruns, order);
+    AD_LAUNCH(k_bin_key3, big, 256, 0, g->stream, sorted, run_of, run_start, order, nnz, key);
+    AD_TRY(row_ranks(g, key, rank_dev, desc));                             // 5. round robin
+    AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    release();
+    return AD_OK;
+}
+
+// The order through two global radix sorts (any row length).
+static ad_status binned_ranks_sorted(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev,
+                                     uint32_t *bin_dev) {
     const int64_t n = g->n, nnz = g->nnz;
     if (nnz == 0) return AD_OK;
     if (n >= ((int64_t)1 << (64 - kBinBits))) return fail(AD_ERR_INVALID_ARG, "graph too large for binned ranks");

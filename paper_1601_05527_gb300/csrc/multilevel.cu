@@ -554,7 +554,7 @@ static ad_status ml_upward(ad_ml_t ml, const std::vector<double> &r, uint8_t *ke
                     if (!sub->rho) st = dalloc_t(sub, sub->m + 1, &sub->rho);
                     if (st == AD_OK)
                         st = algebraic_distance(sub, ml->p.R, ml->p.k, ml->p.omega, ml->p.seed, (uint32_t)(2 * l + 1),
-                                                ml->p.storage, 0, sub->rho);
+                                                ml->p.storage, AD_DIST_PERSISTENT, sub->rho);
                     uint8_t *ks = nullptr;
                     if (st == AD_OK) st = dalloc_t(sub, sub->m + 1, &ks);
                     int64_t k = 0;
@@ -624,7 +624,9 @@ extern "C" ad_status ad_ml_build(ad_graph_t g, const ad_ml_params *params, ad_ml
         ml->lv.push_back(lev);
         ad_ml_s::Level &v = ml->lv.back();
         if (!cur->rho) { if ((st = dalloc_t(cur, cur->m + 1, &cur->rho)) != AD_OK) break; }
-        if ((st = algebraic_distance(cur, p.R, p.k, p.omega, p.seed, (uint32_t)(2 * l), p.storage, 0, cur->rho)) != AD_OK)
+        // every level is relaxed in one persistent launch (init, k sweeps, distances)
+        if ((st = algebraic_distance(cur, p.R, p.k, p.omega, p.seed, (uint32_t)(2 * l), p.storage, AD_DIST_PERSISTENT,
+                                     cur->rho)) != AD_OK)
             break;
         cur->have_rho = true;
         cur->rho_version++;

@@ -1024,6 +1024,20 @@ static ad_status entry_ranks(ad_graph_t g, ad_graph_s::SelCache *c, const uint32
     return AD_OK;
 }
 
+// Rank of every CSR entry inside its row by (key, position), ascending, for
+// caller keys (rank_out[nnz], device; desc_scratch[nnz] receives the
+// descending ranks, which the ranking yields as well).
+ad_status row_ranks(ad_graph_t g, const uint32_t *ekey, uint32_t *rank_out, uint32_t *desc_scratch) {
+    AD_TRY(ensure_degree_classes(g));
+    ad_graph_s::SelCache *c = nullptr;
+    AD_TRY(sel_cache(g, &c));
+    AD_TRY(rank_lists(g, c));
+    RankOut out;
+    out.asc = rank_out;
+    out.desc = desc_scratch;
+    return entry_ranks(g, c, ekey, out);
+}
+
 // Ranks of every CSR entry in both orders, gathered per edge: the info of
 // Alg. 2.  For the handle's own distances the result is kept until they change.
 static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, int4 **info_out) {

@@ -123,6 +123,104 @@ ad_status sweep_step(ad_graph_t g, ad_storage storage, int32_t R, double omega, 
     return dispatch_storage(g, storage, cf, true, a, 2 * 8 * (size_t)cf.stride * sizeof(float));
 }
 
+// ----------------------------------------------------------------------------
+// Persistent form (k_relax): init, k sweeps and distances in one cooperative
+// launch with bounded grid barriers between sweeps.  A barrier that runs out
+// leaves AD_ERR_TIMEOUT in the handle's flag, which a direct call reads back
+// (inside a stream capture the call cannot wait, and the flag is not read).
+// ----------------------------------------------------------------------------
+static ad_status relax_storage(ad_graph_t g, ad_storage storage, const Config &cf, RelaxArgs &r) {
+    switch (storage) {
+        case AD_STORAGE_BF16: return relax_bf16(g, cf, r);
+        case AD_STORAGE_FP16: return relax_f16(g, cf, r);
+        case AD_STORAGE_Q16: return relax_q16(g, cf, r);
+        default: return relax_f32(g, cf, r);
+    }
+}
+
+static ad_status relax_persistent(ad_graph_t g, const Config &cf, int32_t R, int32_t k, double omega, uint64_t seed,
+                                  uint32_t stream_id, ad_storage storage, int32_t flags, float *rho_dev,
+                                  const RowPlan &sp, const RowPlan &dp) {
+    AD_TRY(ensure(g, g->relax_sync, (kBarrierSlots + 4) * sizeof(unsigned int)));
+    unsigned int *sync = static_cast<unsigned int *>(g->relax_sync.ptr);
+    AD_CUDA_TRY(cudaMemsetAsync(sync, 0, (kBarrierSlots + 4) * sizeof(unsigned int), g->stream));
+    RelaxArgs r;
+    memset(&r, 0, sizeof(r));
+    SweepArgs &a = r.s;
+    a.rp = g->rp; a.col = g->col; a.w = g->w; a.Dinv = g->Dinv; a.D = g->D;
+    a.upos = g->upos; a.eoff = g->eoff;
+    a.part = static_cast<float *>(g->part.ptr);
+    a.stride = cf.stride; a.nchunks = cf.nchunks; a.R = R;
+    a.omega = (float)omega;
+    a.normalize = (flags & AD_DIST_NORMALIZE) ? 1 : 0;
+    a.voff = g->voff; a.G = 1; a.blocked = 0;
+    a.anchor = g->anchor;
+    r.d = a;
+    fill_plan(r.s, sp);
+    fill_plan(r.d, dp);
+    r.d.rho = rho_dev;
+    r.n = g->n;
+    r.k = k;
+    r.x0 = g->x0.ptr;
+    r.x1 = g->x1.ptr;
+    const size_t mm_words = (size_t)(k > 0 ? k : 1) * cf.stride;
+    r.mm_min = static_cast<uint32_t *>(g->mm.ptr);
+    r.mm_max = r.mm_min + mm_words;
+    r.seed_lo = (uint32_t)seed;
+    r.seed_hi = (uint32_t)(seed >> 32);
+    r.stream_id = stream_id;
+    r.bar = sync;
+    r.err = reinterpret_cast<int *>(sync + kBarrierSlots);
+    r.polls = AD_BARRIER_POLLS;
+    r.extra = 0;
+    AD_TRY(relax_storage(g, storage, cf, r));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    AD_CUDA_TRY(cudaStreamIsCapturing(g->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+        int err = 0;
+        AD_TRY(copy_out(g, &err, r.err, sizeof(int)));
+        if (err != 0) return fail((ad_status)err, "a grid barrier of the persistent relaxation ran out of time");
+    }
+    return AD_OK;
+}
+
+// Self-test of the bounded grid barrier: a cooperative launch of two CTAs
+// whose barrier waits for one arrival that never comes.
+static __device__ unsigned int g_selftest_sync[kBarrierSlots + 4];
+
+__global__ void k_barrier_selftest(RelaxArgs r) {
+    if (grid_barrier(r, 1) && threadIdx.x == 0) atomicAdd(r.bar + kBarrierSlots + 1, 1u);   // CTAs that passed
+}
+
+}  // namespace ad
+
+extern "C" ad_status ad_selftest_barrier_timeout(void *stream, uint32_t polls, int32_t *status_out) {
+    using namespace ad;
+    if (!status_out) return fail(AD_ERR_INVALID_ARG, "status_out is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *p = nullptr;
+    AD_CUDA_TRY(cudaGetSymbolAddress(&p, g_selftest_sync));
+    unsigned int *sync = static_cast<unsigned int *>(p);
+    AD_CUDA_TRY(cudaMemsetAsync(sync, 0, (kBarrierSlots + 4) * sizeof(unsigned int), st));
+    RelaxArgs r;
+    memset(&r, 0, sizeof(r));
+    r.bar = sync;
+    r.err = reinterpret_cast<int *>(sync + kBarrierSlots);
+    r.polls = polls;
+    r.extra = 1;
+    void *args[] = {&r};
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    AD_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(2), dim3(64), args, 0, st));
+    unsigned int h[kBarrierSlots + 4] = {};
+    AD_CUDA_TRY(cudaMemcpyAsync(h, sync, sizeof(h), cudaMemcpyDeviceToHost, st));
+    AD_CUDA_TRY(cudaStreamSynchronize(st));
+    *status_out = (int32_t)h[kBarrierSlots];
+    if (h[kBarrierSlots + 1] != 0) return fail(AD_ERR_STATE, "a CTA passed a barrier that could not complete");
+    return AD_OK;
+}
+
+namespace ad {
+
 ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, uint64_t seed,
                              uint32_t stream_id, ad_storage storage, int32_t flags, float *rho_dev,
                              const KeepSpec *keep) {
@@ -144,6 +242,11 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
     AD_TRY(get_plan(g, groups, false, &sp));
     AD_TRY(get_plan(g, groups, true, &dp));
     AD_TRY(ensure(g, g->part, (size_t)(sp->n_big > 0 ? sp->n_big : 1) * cf.stride * sizeof(float)));
+
+    // small single graphs (or on request): the whole computation in one persistent launch
+    const bool persist = g->G == 1 && !keep && !g->profiling &&
+                         ((flags & AD_DIST_PERSISTENT) || g->nnz <= kPersistMaxNnz);
+    if (persist) return relax_persistent(g, cf, R, k, omega, seed, stream_id, storage, flags, rho_dev, *sp, *dp);
 
     // init
     {

@@ -22,6 +22,7 @@
 #pragma once
 #include "ad_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -124,8 +125,9 @@ __device__ __forceinline__ TaskIter task_iter(int64_t n_tasks, int64_t wid, int6
 // degree 0 are skipped.
 // ----------------------------------------------------------------------------
 template <typename T>
-__global__ void k_init(const int64_t *__restrict__ rp, int64_t n, int32_t stride, uint32_t seed_lo,
-                       uint32_t seed_hi, uint32_t stream_id, const int64_t *voff, int G, T *__restrict__ x) {
+__device__ __forceinline__ void init_rows(const int64_t *__restrict__ rp, int64_t n, int32_t stride, uint32_t seed_lo,
+                                          uint32_t seed_hi, uint32_t stream_id, const int64_t *voff, int G,
+                                          T *__restrict__ x) {
     const int32_t quads = stride / 4;
     const int64_t total = n * quads;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -145,6 +147,12 @@ __global__ void k_init(const int64_t *__restrict__ rp, int64_t n, int32_t stride
             *reinterpret_cast<uint2 *>(dst) = p;
         }
     }
+}
+
+template <typename T>
+__global__ void k_init(const int64_t *__restrict__ rp, int64_t n, int32_t stride, uint32_t seed_lo,
+                       uint32_t seed_hi, uint32_t stream_id, const int64_t *voff, int G, T *__restrict__ x) {
+    init_rows<T>(rp, n, stride, seed_lo, seed_hi, stream_id, voff, G, x);
 }
 
 // ----------------------------------------------------------------------------
@@ -171,6 +179,17 @@ __device__ __forceinline__ void accumulate(float *acc, const float *f, float w) 
         else add_f32x2(acc[e], acc[e + 1], f[e], f[e + 1]);
     }
 }
+// Loads of the test-vector block.  Separate launches read it through the
+// read-only path; a persistent launch (k_relax) rewrites it between sweeps, so
+// there it is read coherently from L2, and the per-sweep scale and centre come
+// from shared memory.
+template <bool P>
+__device__ __forceinline__ uint4 ldx(const uint4 *p) { return P ? __ldcg(p) : __ldg(p); }
+template <bool P>
+__device__ __forceinline__ float4 ldac(const float *p) {
+    return P ? *reinterpret_cast<const float4 *>(p) : __ldg(reinterpret_cast<const float4 *>(p));
+}
+
 template <typename T, int LPR, int CPL>
 struct Lane {
     static constexpr int V = Store<T>::V;
@@ -186,7 +205,7 @@ struct Lane {
 // any of them, so that enough requests are in flight to cover the L2 latency.
 // W: edge weights present; without them no weight is read or broadcast and
 // the rows are plainly added (the same sums as fmaf with weight 1).
-template <typename T, int LPR, int CPL, bool W>
+template <typename T, int LPR, int CPL, bool W, bool P>
 __device__ __forceinline__ void warp_gather_w(const SweepArgs &a, int64_t p0, int64_t p1, int lane, int grp,
                                               int gl, float (&acc)[CPL * Store<T>::V]) {
     using L = Lane<T, LPR, CPL>;
@@ -224,7 +243,7 @@ __device__ __forceinline__ void warp_gather_w(const SweepArgs &a, int64_t p0, in
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
                     const int q = gl + c * LPR;
-                    v[u][c] = (src < cnt && q < a.nchunks) ? __ldg(X + (int64_t)nb * row_q + q) : make_uint4(0, 0, 0, 0);
+                    v[u][c] = (src < cnt && q < a.nchunks) ? ldx<P>(X + (int64_t)nb * row_q + q) : make_uint4(0, 0, 0, 0);
                 }
             }
 #pragma unroll
@@ -239,20 +258,20 @@ __device__ __forceinline__ void warp_gather_w(const SweepArgs &a, int64_t p0, in
     }
 }
 
-template <typename T, int LPR, int CPL>
+template <typename T, int LPR, int CPL, bool P>
 __device__ __forceinline__ void warp_gather(const SweepArgs &a, int64_t p0, int64_t p1, int lane, int grp,
                                             int gl, float (&acc)[CPL * Store<T>::V]) {
     if (!a.w) {   // the weighted loop reads a.w: it is reached only with weights present
-        warp_gather_w<T, LPR, CPL, false>(a, p0, p1, lane, grp, gl, acc);
+        warp_gather_w<T, LPR, CPL, false, P>(a, p0, p1, lane, grp, gl, acc);
         return;
     }
-    warp_gather_w<T, LPR, CPL, true>(a, p0, p1, lane, grp, gl, acc);
+    warp_gather_w<T, LPR, CPL, true, P>(a, p0, p1, lane, grp, gl, acc);
 }
 
 // Gather-accumulate a short row (<= kSmallUnroll entries per round) with one
 // lane group: all of its column indices, then all row loads, then the sums.
 constexpr int kSmallUnroll = AD_SWEEP_UB;
-template <typename T, int LPR, int CPL, bool W>
+template <typename T, int LPR, int CPL, bool W, bool P>
 __device__ __forceinline__ void group_gather_w(const SweepArgs &a, int64_t p0, int64_t p1, int gl,
                                                float (&acc)[CPL * Store<T>::V]) {
     constexpr int V = Store<T>::V;
@@ -274,7 +293,7 @@ __device__ __forceinline__ void group_gather_w(const SweepArgs &a, int64_t p0, i
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 const int q = gl + c * LPR;
-                v[u][c] = (base + u < p1 && q < a.nchunks) ? __ldg(X + (int64_t)nb[u] * row_q + q) : make_uint4(0, 0, 0, 0);
+                v[u][c] = (base + u < p1 && q < a.nchunks) ? ldx<P>(X + (int64_t)nb[u] * row_q + q) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
         for (int u = 0; u < UB; ++u)
@@ -287,14 +306,14 @@ __device__ __forceinline__ void group_gather_w(const SweepArgs &a, int64_t p0, i
     }
 }
 
-template <typename T, int LPR, int CPL>
+template <typename T, int LPR, int CPL, bool P>
 __device__ __forceinline__ void group_gather(const SweepArgs &a, int64_t p0, int64_t p1, int gl,
                                              float (&acc)[CPL * Store<T>::V]) {
     if (!a.w) {   // the weighted loop reads a.w: it is reached only with weights present
-        group_gather_w<T, LPR, CPL, false>(a, p0, p1, gl, acc);
+        group_gather_w<T, LPR, CPL, false, P>(a, p0, p1, gl, acc);
         return;
     }
-    group_gather_w<T, LPR, CPL, true>(a, p0, p1, gl, acc);
+    group_gather_w<T, LPR, CPL, true, P>(a, p0, p1, gl, acc);
 }
 
 // Sum over the G groups of a warp (butterfly: every group ends with the total).
@@ -307,18 +326,18 @@ __device__ __forceinline__ void reduce_groups(float (&acc)[E]) {
 }
 
 // Epilogue of a row: z = (1-omega) s_i + omega Dinv_i S, store a (z - c), track min/max.
-template <typename T, int LPR, int CPL>
+template <typename T, int LPR, int CPL, bool P = false>
 __device__ __forceinline__ void load_own(const SweepArgs &a, int64_t row, int gl, uint4 (&own)[CPL]) {
     const uint4 *X = reinterpret_cast<const uint4 *>(a.x_in);
     const int64_t row_q = a.stride / Store<T>::V;
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
         const int q = gl + c * LPR;
-        own[c] = q < a.nchunks ? __ldg(X + row * row_q + q) : make_uint4(0, 0, 0, 0);
+        own[c] = q < a.nchunks ? ldx<P>(X + row * row_q + q) : make_uint4(0, 0, 0, 0);
     }
 }
 
-template <typename T, int LPR, int CPL>
+template <typename T, int LPR, int CPL, bool P = false>
 __device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, int gl, const uint4 (&own)[CPL],
                                              const float (&S)[CPL * Store<T>::V], const float *acg,
                                              float (&mn)[CPL * Store<T>::V], float (&mx)[CPL * Store<T>::V]) {
@@ -335,8 +354,8 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, in
             Store<T>::unpack(own[c], y);
 #pragma unroll
             for (int e4 = 0; e4 < V / 4; ++e4) {   // scale and centre of the row's graph (the same line for every row)
-                const float4 av = __ldg(reinterpret_cast<const float4 *>(acg + q * V) + e4);
-                const float4 cv = __ldg(reinterpret_cast<const float4 *>(acg + a.stride + q * V) + e4);
+                const float4 av = ldac<P>(acg + q * V + 4 * e4);
+                const float4 cv = ldac<P>(acg + a.stride + q * V + 4 * e4);
                 A[4 * e4] = av.x; A[4 * e4 + 1] = av.y; A[4 * e4 + 2] = av.z; A[4 * e4 + 3] = av.w;
                 C[4 * e4] = cv.x; C[4 * e4 + 1] = cv.y; C[4 * e4 + 2] = cv.z; C[4 * e4 + 3] = cv.w;
             }
@@ -354,7 +373,7 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs &a, int64_t row, in
 
 // Scale a = 1 / (max - min) of the previous sweep's stored values for the
 // lane's elements (1 before the first sweep, 0 for a vector with max == min).
-template <typename T, int LPR, int CPL>
+template <typename T, int LPR, int CPL, bool P = false>
 __device__ __forceinline__ void load_scale(const uint32_t *pmin, const uint32_t *pmax, int gl,
                                            float (&A)[CPL * Store<T>::V]) {
     // pmin / pmax point at the slots of the row's graph (nullptr: no rescale yet)
@@ -366,7 +385,7 @@ __device__ __forceinline__ void load_scale(const uint32_t *pmin, const uint32_t 
             const int r = (gl + c * LPR) * V + e;
             float av = 1.f;
             if (pmin) {   // FP32 on purpose: FP64 division runs on a very narrow pipe on this part
-                const float lo = ord2f(pmin[r]), hi = ord2f(pmax[r]);
+                const float lo = ord2f(P ? __ldcg(pmin + r) : pmin[r]), hi = ord2f(P ? __ldcg(pmax + r) : pmax[r]);
                 av = hi > lo ? 1.f / (hi - lo) : 0.f;
             }
             A[c * V + e] = av;
@@ -473,16 +492,19 @@ __device__ __forceinline__ void sum_partials(const SweepArgs &a, int64_t t0, int
 template <typename T>
 constexpr int sweep_minb() { return sizeof(T) == 4 ? AD_SWEEP_MINB : AD_SWEEP_MINB16; }
 
-template <typename T, int LPR, int CPL>
-__global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
+// The tasks of one sweep on this CTA, then the CTA's min/max to the sweep's
+// slots.  P: inside the persistent launch (acs = the scale and centre of the
+// single graph in shared memory).
+template <typename T, int LPR, int CPL, bool P>
+__device__ __forceinline__ void sweep_tasks(const SweepArgs &a, float *sm, const float *acs) {
     using L = Lane<T, LPR, CPL>;
     constexpr int V = L::V, E = L::E, G = L::G;
-    extern __shared__ float sm[];   // [2][warps][stride]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int grp = lane / LPR, gl = lane % LPR;
 
     LaneStats<T, LPR, CPL> ls;
     ls.enter(a, gl, 0, false);
+    if (P) ls.acg = acs;
     auto row_graph = [&](int64_t row) { return a.G > 1 ? graph_of(a.voff, a.G, row) : 0; };
 
     const int64_t W = (int64_t)gridDim.x * nwarps;
@@ -497,7 +519,7 @@ __global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
             const int32_t c = a.big_chunk[task];
             const int64_t rb = a.rp[row], re = a.rp[row + 1];
             const int64_t p0 = rb + (int64_t)c * kChunk, p1 = min(re, p0 + kChunk);
-            warp_gather<T, LPR, CPL>(a, p0, p1, lane, grp, gl, acc);
+            warp_gather<T, LPR, CPL, P>(a, p0, p1, lane, grp, gl, acc);
             reduce_groups<LPR, E>(acc);
             float *part = a.part + task * (int64_t)a.stride;
             if (grp == 0) {
@@ -521,12 +543,12 @@ __global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
                 __threadfence();
                 // group g sums partials g, g + G, ... (fixed order); then the groups' sums are added
                 uint4 own[CPL];
-                load_own<T, LPR, CPL>(a, row, gl, own);
+                load_own<T, LPR, CPL, P>(a, row, gl, own);
                 float S[E];
                 sum_partials<T, LPR, CPL>(a, t0, nchunk, grp, gl, S);
                 if (grp == 0) {
                     ls.enter(a, gl, row_graph(row), true);
-                    row_epilogue<T, LPR, CPL>(a, row, gl, own, S, ls.acg, ls.mn, ls.mx);
+                    row_epilogue<T, LPR, CPL, P>(a, row, gl, own, S, ls.acg, ls.mn, ls.mx);
                 }
                 if (lane == 0) a.big_counter[t0] = 0u;
             }
@@ -534,12 +556,12 @@ __global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
             // ---- one row, whole warp
             const int64_t row = a.medium_row[task - a.n_big];
             uint4 own[CPL];
-            load_own<T, LPR, CPL>(a, row, gl, own);
-            warp_gather<T, LPR, CPL>(a, a.rp[row], a.rp[row + 1], lane, grp, gl, acc);
+            load_own<T, LPR, CPL, P>(a, row, gl, own);
+            warp_gather<T, LPR, CPL, P>(a, a.rp[row], a.rp[row + 1], lane, grp, gl, acc);
             reduce_groups<LPR, E>(acc);
             if (grp == 0) {
                 ls.enter(a, gl, row_graph(row), true);
-                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.acg, ls.mn, ls.mx);
+                row_epilogue<T, LPR, CPL, P>(a, row, gl, own, acc, ls.acg, ls.mn, ls.mx);
             }
         } else {
             // ---- G low-degree rows, one per lane group
@@ -547,10 +569,10 @@ __global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
             if (si < a.n_small_rows) {
                 const int64_t row = a.small_row[si];
                 uint4 own[CPL];
-                load_own<T, LPR, CPL>(a, row, gl, own);
-                group_gather<T, LPR, CPL>(a, a.rp[row], a.rp[row + 1], gl, acc);
+                load_own<T, LPR, CPL, P>(a, row, gl, own);
+                group_gather<T, LPR, CPL, P>(a, a.rp[row], a.rp[row + 1], gl, acc);
                 ls.enter(a, gl, row_graph(row), true);
-                row_epilogue<T, LPR, CPL>(a, row, gl, own, acc, ls.acg, ls.mn, ls.mx);
+                row_epilogue<T, LPR, CPL, P>(a, row, gl, own, acc, ls.acg, ls.mn, ls.mx);
             }
         }
     }
@@ -605,6 +627,12 @@ __global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
     }
 }
 
+template <typename T, int LPR, int CPL>
+__global__ void __launch_bounds__(256, sweep_minb<T>()) k_sweep(SweepArgs a) {
+    extern __shared__ float sm[];   // [2][warps][stride]
+    sweep_tasks<T, LPR, CPL, false>(a, sm, nullptr);
+}
+
 // ----------------------------------------------------------------------------
 // Edge distance: for every upper entry (i, j > i) of the CSR, edge id e =
 // eoff[i] + (p - upos[i]), rho_e = sqrt(sum_r a_r^2 (y_i^r - y_j^r)^2).
@@ -639,7 +667,7 @@ __device__ __forceinline__ void group_sums(float (&s)[K], int gl, unsigned gmask
     }
 }
 
-template <typename T, int LPR, int CPL>
+template <typename T, int LPR, int CPL, bool P>
 __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64_t p0, int64_t p1, int step,
                                           int first, int gl, unsigned gmask, const float (&A2)[CPL * Store<T>::V]) {
     constexpr int V = Store<T>::V, E = CPL * V;
@@ -651,7 +679,7 @@ __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
         const int q = gl + c * LPR;
-        if (q < a.nchunks) Store<T>::unpack(__ldg(X + row * row_q + q), yi + c * V);
+        if (q < a.nchunks) Store<T>::unpack(ldx<P>(X + row * row_q + q), yi + c * V);
         else {
 #pragma unroll
             for (int e = 0; e < V; ++e) yi[c * V + e] = 0.f;
@@ -673,7 +701,7 @@ __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 const int q = gl + c * LPR;
-                v[u][c] = (pb + (int64_t)u * step < p1 && q < a.nchunks) ? __ldg(X + (int64_t)jn[u] * row_q + q)
+                v[u][c] = (pb + (int64_t)u * step < p1 && q < a.nchunks) ? ldx<P>(X + (int64_t)jn[u] * row_q + q)
                                                                           : make_uint4(0, 0, 0, 0);
             }
         float s[UB];
@@ -710,8 +738,8 @@ __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64
     }
 }
 
-template <typename T, int LPR, int CPL>
-__global__ void __launch_bounds__(256, AD_DIST_MINB) k_distance(SweepArgs a) {
+template <typename T, int LPR, int CPL, bool P>
+__device__ __forceinline__ void distance_tasks(const SweepArgs &a) {
     using L = Lane<T, LPR, CPL>;
     constexpr int V = L::V, E = L::E, G = L::G;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -723,7 +751,7 @@ __global__ void __launch_bounds__(256, AD_DIST_MINB) k_distance(SweepArgs a) {
     auto enter = [&](int g) {
         if (g == cg) return;
         cg = g;
-        load_scale<T, LPR, CPL>(a.mm_prev_min ? a.mm_prev_min + (size_t)g * a.stride : nullptr,
+        load_scale<T, LPR, CPL, P>(a.mm_prev_min ? a.mm_prev_min + (size_t)g * a.stride : nullptr,
                                 a.mm_prev_max ? a.mm_prev_max + (size_t)g * a.stride : nullptr, gl, A);
 #pragma unroll
         for (int c = 0; c < CPL; ++c)
@@ -743,20 +771,139 @@ __global__ void __launch_bounds__(256, AD_DIST_MINB) k_distance(SweepArgs a) {
             const int64_t ub = a.upos[row], ue = a.rp[row + 1];
             const int64_t p0 = ub + (int64_t)c * kChunk, p1 = min(ue, p0 + kChunk);
             enter(row_graph(row));
-            edge_rows<T, LPR, CPL>(a, row, p0, p1, G, grp, gl, gmask, A2);
+            edge_rows<T, LPR, CPL, P>(a, row, p0, p1, G, grp, gl, gmask, A2);
         } else if (task < a.n_big + a.n_medium) {
             const int64_t row = a.medium_row[task - a.n_big];
             enter(row_graph(row));
-            edge_rows<T, LPR, CPL>(a, row, a.upos[row], a.rp[row + 1], G, grp, gl, gmask, A2);
+            edge_rows<T, LPR, CPL, P>(a, row, a.upos[row], a.rp[row + 1], G, grp, gl, gmask, A2);
         } else {
             const int64_t si = (task - a.n_big - a.n_medium) * G + grp;
             if (si < a.n_small_rows) {
                 const int64_t row = a.small_row[si];
                 enter(row_graph(row));
-                edge_rows<T, LPR, CPL>(a, row, a.upos[row], a.rp[row + 1], 1, 0, gl, gmask, A2);
+                edge_rows<T, LPR, CPL, P>(a, row, a.upos[row], a.rp[row + 1], 1, 0, gl, gmask, A2);
             }
         }
     }
+}
+
+template <typename T, int LPR, int CPL>
+__global__ void __launch_bounds__(256, AD_DIST_MINB) k_distance(SweepArgs a) {
+    distance_tasks<T, LPR, CPL, false>(a);
+}
+
+// ----------------------------------------------------------------------------
+// Persistent relaxation: the whole of Alg. 1 for a single graph in one
+// cooperative launch -- init, k sweeps, each followed by a grid-wide barrier
+// (the next sweep's rescale needs every CTA's min/max), and the distances.
+// The barrier is a counter that every CTA increments and then polls with an
+// acquire load, at most kBarrierPolls times; a CTA that runs out writes
+// AD_ERR_TIMEOUT to *err and returns, and the others stop at their next
+// barrier once they see the error.
+// ----------------------------------------------------------------------------
+#ifndef AD_BARRIER_POLLS
+#define AD_BARRIER_POLLS (1u << 25)   // with the 32 ns back-off and the loads: a few seconds
+#endif
+
+struct RelaxArgs {
+    SweepArgs s;            // sweep plan and constant fields (x_in / x_out / slots set per sweep)
+    SweepArgs d;            // distance plan
+    int64_t n;              // vertices
+    int32_t k;
+    void *x0, *x1;
+    uint32_t *mm_min, *mm_max;   // [k][stride]
+    uint32_t seed_lo, seed_hi, stream_id;
+    unsigned int *bar;      // [kBarrierSlots] arrival counters, zero before the launch
+    int *err;               // zero before the launch
+    unsigned int polls;     // barrier poll limit
+    unsigned int extra;     // arrivals the barrier waits for beyond the grid (0; > 0 only to test the limit)
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Arrivals are spread over kBarrierSlots counters (CTA b adds to slot b mod
+// kBarrierSlots) so that they do not queue on one address; warp 0 of every
+// CTA sums the slots with acquire loads until the total reaches the target.
+constexpr int kBarrierSlots = 32;
+
+// false: the barrier timed out here or elsewhere (every thread of the CTA gets the same answer)
+__device__ __forceinline__ bool grid_barrier(const RelaxArgs &r, unsigned int phase) {
+    __syncthreads();
+    __shared__ int ok_s;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0) red_release_add_u32(r.bar + (blockIdx.x % kBarrierSlots), 1u);
+        const unsigned int target = (gridDim.x + r.extra) * phase;
+        int ok = 1;
+        unsigned int polls = 0;
+        for (;;) {
+            unsigned int v = ld_acquire_u32(r.bar + lane);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (v >= target) break;
+            if (*(volatile int *)r.err != 0) { ok = 0; break; }
+            if (++polls > r.polls) {
+                if (lane == 0) atomicCAS(r.err, 0, (int)AD_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        if (lane == 0) ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <typename T, int LPR, int CPL>
+__global__ void __launch_bounds__(256, sweep_minb<T>()) k_relax(RelaxArgs r) {
+    constexpr int V = Store<T>::V;
+    extern __shared__ float sm[];   // [2][warps][stride] min/max, then [2][stride] scale and centre
+    float *acs = sm + 2 * (blockDim.x >> 5) * r.s.stride;
+    // x0 <- rand(-0.5, 0.5) on every row of degree > 0
+    init_rows<T>(r.s.rp, r.n, r.s.stride, r.seed_lo, r.seed_hi, r.stream_id, r.s.voff, 1, static_cast<T *>(r.x0));
+    if (!grid_barrier(r, 1)) return;
+    for (int32_t t = 0; t < r.k; ++t) {
+        SweepArgs a = r.s;
+        a.x_in = (t & 1) ? r.x1 : r.x0;
+        a.x_out = (t & 1) ? r.x0 : r.x1;
+        a.mm_prev_min = t > 0 ? r.mm_min + (size_t)(t - 1) * a.stride : nullptr;
+        a.mm_prev_max = t > 0 ? r.mm_max + (size_t)(t - 1) * a.stride : nullptr;
+        a.mm_min = r.mm_min + (size_t)t * a.stride;
+        a.mm_max = r.mm_max + (size_t)t * a.stride;
+        // scale and centre of this sweep (what k_scale_center computes), per CTA
+        const uint4 *xa = reinterpret_cast<const uint4 *>(a.x_in) + (int64_t)__ldg(a.anchor) * (a.stride / V);
+        for (int q = threadIdx.x; q < a.stride / V; q += blockDim.x) {
+            float f[V];
+            Store<T>::unpack(__ldcg(xa + q), f);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const int rr = q * V + e;
+                float av = 1.f;
+                if (a.mm_prev_min) {
+                    const float lo = ord2f(__ldcg(a.mm_prev_min + rr)), hi = ord2f(__ldcg(a.mm_prev_max + rr));
+                    av = hi > lo ? 1.f / (hi - lo) : 0.f;
+                }
+                acs[rr] = av;
+                acs[a.stride + rr] = f[e];
+            }
+        }
+        __syncthreads();
+        sweep_tasks<T, LPR, CPL, true>(a, sm, acs);
+        if (!grid_barrier(r, (unsigned int)t + 2)) return;
+    }
+    SweepArgs d = r.d;
+    d.x_in = (r.k & 1) ? r.x1 : r.x0;
+    d.mm_prev_min = r.k > 0 ? r.mm_min + (size_t)(r.k - 1) * d.stride : nullptr;
+    d.mm_prev_max = r.k > 0 ? r.mm_max + (size_t)(r.k - 1) * d.stride : nullptr;
+    distance_tasks<T, LPR, CPL, true>(d);
 }
 
 struct Config {
@@ -821,11 +968,52 @@ ad_status dispatch(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &
 }
 
 
+// Persistent launch of k_relax: every CTA co-resident (cooperative launch),
+// as many as fit or as the larger of the two plans can use.
+template <typename T, int LPR, int CPL>
+ad_status launch_relax(ad_graph_t g, const Config &cf, RelaxArgs &r) {
+    const size_t smem = (2 * 8 + 2) * (size_t)r.s.stride * sizeof(float);
+    int per_sm = 0;
+    AD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_relax<T, LPR, CPL>, 256, smem));
+    if (per_sm < 1) return fail(AD_ERR_CUDA, "the persistent relaxation kernel does not fit on an SM");
+    if (cf.per_sm > 0 && cf.per_sm < per_sm) per_sm = cf.per_sm;
+    int64_t blocks = (int64_t)per_sm * g->num_sms;
+    const int64_t need = (std::max(r.s.n_tasks, r.d.n_tasks) + 7) / 8;
+    if (blocks > need) blocks = need > 0 ? need : 1;
+    void *args[] = {&r};
+    ::ad::g_launches.fetch_add(1, std::memory_order_relaxed);
+    AD_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_relax<T, LPR, CPL>, dim3((unsigned)blocks), dim3(256), args,
+                                            smem, g->stream));
+    return AD_OK;
+}
+
+template <typename T>
+ad_status relax_dispatch(ad_graph_t g, const Config &cf, RelaxArgs &r) {
+    using std::integral_constant;
+    auto run = [&](auto lpr_c, auto cpl_c) -> ad_status {
+        return launch_relax<T, decltype(lpr_c)::value, decltype(cpl_c)::value>(g, cf, r);
+    };
+    switch (cf.lpr * 100 + cf.cpl) {
+        case 101: return run(integral_constant<int, 1>{}, integral_constant<int, 1>{});
+        case 201: return run(integral_constant<int, 2>{}, integral_constant<int, 1>{});
+        case 401: return run(integral_constant<int, 4>{}, integral_constant<int, 1>{});
+        case 801: return run(integral_constant<int, 8>{}, integral_constant<int, 1>{});
+        case 1601: return run(integral_constant<int, 16>{}, integral_constant<int, 1>{});
+        case 3201: return run(integral_constant<int, 32>{}, integral_constant<int, 1>{});
+        case 3202: return run(integral_constant<int, 32>{}, integral_constant<int, 2>{});
+        default: return fail(AD_ERR_INVALID_ARG, "the persistent relaxation takes the natural lane shapes only");
+    }
+}
+
 // one instantiation per storage type, each in its own translation unit
 ad_status dispatch_f32(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &a, int64_t n_tasks, size_t smem);
 ad_status dispatch_bf16(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &a, int64_t n_tasks, size_t smem);
 ad_status dispatch_f16(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &a, int64_t n_tasks, size_t smem);
 ad_status dispatch_q16(ad_graph_t g, const Config &cf, bool sweep, const SweepArgs &a, int64_t n_tasks, size_t smem);
+ad_status relax_f32(ad_graph_t g, const Config &cf, RelaxArgs &r);
+ad_status relax_bf16(ad_graph_t g, const Config &cf, RelaxArgs &r);
+ad_status relax_f16(ad_graph_t g, const Config &cf, RelaxArgs &r);
+ad_status relax_q16(ad_graph_t g, const Config &cf, RelaxArgs &r);
 ad_status launch_init(ad_graph_t g, ad_storage storage, int blocks, int32_t stride, uint64_t seed, uint32_t stream_id,
                       void *x);
 

@@ -278,3 +278,48 @@ def test_autotuned_shape_keeps_the_distances(storage, R):
         assert_rho_close(after, ref_rho(g, R, 12, 0.5, seed=3))
     else:
         assert rho_error(after, before.astype(np.float64)) < 0.05
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_persistent_launch_equals_separate_launches(storage):
+    """AD_DIST_PERSISTENT relaxes a single graph in one cooperative launch
+    (init, k sweeps with grid-wide barriers, distances); profiling forces one
+    launch per sweep.  The arithmetic is the same, so the distances must be
+    bit-identical, and the FP32 ones within tolerance of the oracle."""
+    L = lib()
+    g = weighted(graphgen.rmat(13, 16, seed=12), seed=3)
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, g.weight)
+    a = np.zeros(g.m, np.float32)
+    L.ad_algebraic_distance(h, 32, 20, 0.5, 7, 0, storage, L.AD_DIST_PERSISTENT, a)
+    L.ad_graph_set_profiling(h, True)
+    b = np.zeros(g.m, np.float32)
+    L.ad_algebraic_distance(h, 32, 20, 0.5, 7, 0, storage, 0, b)
+    L.ad_graph_set_profiling(h, False)
+    L.ad_graph_destroy(h)
+    np.testing.assert_array_equal(a, b)
+    if storage == "fp32":
+        assert_rho_close(a, ref_rho(g, 32, 20, 0.5, seed=7))
+
+
+def test_persistent_launch_on_a_larger_graph():
+    """AD_DIST_PERSISTENT on a graph whose sweeps use every SM."""
+    L = lib()
+    g = graphgen.rmat(17, 16, seed=5)
+    assert g.nnz > (1 << 21)
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
+    a = np.zeros(g.m, np.float32)
+    L.ad_algebraic_distance(h, 32, 6, 0.5, 3, 0, "fp32", L.AD_DIST_PERSISTENT, a)
+    b = np.zeros(g.m, np.float32)
+    L.ad_algebraic_distance(h, 32, 6, 0.5, 3, 0, "fp32", 0, b)
+    L.ad_graph_destroy(h)
+    np.testing.assert_array_equal(a, b)
+    assert_rho_close(a, ref_rho(g, 32, 6, 0.5, seed=3))
+
+
+def test_grid_barrier_wait_is_bounded():
+    """A grid-wide barrier that can never complete ends with AD_ERR_TIMEOUT
+    after its poll limit instead of hanging, and the context stays usable."""
+    L = lib()
+    assert L.ad_selftest_barrier_timeout(polls=2000) == 8      # AD_ERR_TIMEOUT
+    g = graphgen.grid2d(16, 16)
+    assert_rho_close(gpu_rho(g, 8, 10, 0.5, seed=2), ref_rho(g, 8, 10, 0.5, seed=2))
