@@ -378,6 +378,8 @@ ad_status select_per_node_fit_ranked(ad_graph_t g, const uint32_t *rank_dev, dou
                                      int64_t *n_kept, double *e_used);
 ad_status select_local_degree(ad_graph_t g, double fraction, uint8_t *keep_dev, int64_t *n_kept, double *e_used);
 ad_status row_ranks(ad_graph_t g, const uint32_t *ekey, uint32_t *rank_out, uint32_t *desc_scratch);
+constexpr int64_t kLongRowDegree = 512;   // long_rows(): the rows of degree above this
+ad_status long_rows(ad_graph_t g, const int64_t **rows, int64_t *count);
 
 // SparsifyB order (binned.cu)
 ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint32_t *rank_dev,

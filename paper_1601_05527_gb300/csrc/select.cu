@@ -1038,6 +1038,19 @@ ad_status row_ranks(ad_graph_t g, const uint32_t *ekey, uint32_t *rank_out, uint
     return entry_ranks(g, c, ekey, out);
 }
 
+// The rows of degree above 512, by increasing id (device array, owned by the
+// handle's selection cache; valid until the handle is destroyed).
+ad_status long_rows(ad_graph_t g, const int64_t **rows, int64_t *count) {
+    AD_TRY(ensure_degree_classes(g));
+    ad_graph_s::SelCache *c = nullptr;
+    AD_TRY(sel_cache(g, &c));
+    AD_TRY(rank_lists(g, c));
+    constexpr int NC = kRankClasses - 1;   // classes NC-2 and NC-1 (degree > 512) are adjacent in one array
+    *rows = c->rows[NC - 2];
+    *count = c->nrows[NC - 2] + c->nrows[NC - 1];
+    return AD_OK;
+}
+
 // Ranks of every CSR entry in both orders, gathered per edge: the info of
 // Alg. 2.  For the handle's own distances the result is kept until they change.
 static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, int4 **info_out) {

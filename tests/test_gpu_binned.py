@@ -1,10 +1,11 @@
 """GPU parity of SparsifyB (Alg. 3, the binned "mixture" selection of Sec. 4).
 
 The oracle computes each node's mean, sigma, bin width and bins with
-sequential FP64 sums in CSR order; the GPU sums the same FP64 values over the
-lanes of a warp.  Bins are therefore compared entry by entry with the
-oracle's: a bin may differ only where (rho - min) / h lies within rounding of
-an integer, and the share of such rows is bounded.  On every row whose bins
+sequential FP64 sums in CSR order; the GPU adds the terms of the same sums in
+FP32 pairs (error-free transformations, relative error near 2^-48) and
+combines the pairs in FP64.  Bins are therefore compared entry by entry with
+the oracle's: a bin may differ only where (rho - min) / h lies within rounding
+of an integer, and the share of such rows is bounded.  On every row whose bins
 agree, the selection ranks (Philox order inside and across bins, round robin)
 must equal the oracle's exactly; where no bin differs, the kept edge set, its
 size and the fitted e must be the oracle's exactly."""
@@ -131,5 +132,30 @@ def test_full_size_rmat20_binned():
         flips, rows = check_bins_and_ranks(L, h, g, s, 9, max_flip_row_share=1e-5)
         print(f"bin flips against the FP64 oracle: {flips} entries in {rows} rows of {int((g.degrees() > 0).sum())}")
         check_keep(L, h, g, s, 0.3, 9, flips)
+    finally:
+        L.ad_graph_destroy(h)
+
+
+def test_binned_rows_of_many_bins():
+    """A hub whose distances put most entries on one value and spread the rest
+    thinly: the hub row has ~170 non-empty bins, so the direct count of the
+    round-robin ranks (cost d * bins per row) gives way to the per-row rank
+    pass.  Both routes must give the oracle's ranks."""
+    L = lib()
+    n = 20001
+    g = graphgen.from_edges(n, np.zeros(n - 1, np.int64), np.arange(1, n))
+    rng = np.random.default_rng(11)
+    s = np.full(g.m, 0.5, np.float32)
+    spread = rng.random(g.m) < 0.02
+    s[spread] = rng.random(int(spread.sum())).astype(np.float32)
+    _, ref_bins = oracle.binned_ranks(g.row_ptr, g.col, s.astype(np.float64), 5, return_bins=True)
+    rows = np.repeat(np.arange(g.n), g.degrees())
+    work = sum(int(g.degrees()[i]) * len(np.unique(ref_bins[rows == i])) for i in np.unique(rows[g.degrees()[rows] > 1]))
+    work += int((g.degrees() == 1).sum())
+    assert work > 64 * g.nnz                  # the case this test is for
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
+    try:
+        flips, _ = check_bins_and_ranks(L, h, g, s, 5)
+        check_keep(L, h, g, s, 0.3, 5, flips)
     finally:
         L.ad_graph_destroy(h)
