@@ -273,6 +273,20 @@ ad_status ad_sparsify(ad_graph_t g, double fraction, ad_mode mode, ad_scope scop
                       int64_t *n_kept, double *e_used);
 
 /*
+ * Alg. 2 (per-node scope) in both orders at once on the scores of the last
+ * ad_algebraic_distance call: keep_local[m] receives the AD_MODE_LOCAL
+ * selection and keep_global[m] the AD_MODE_GLOBAL one, each exactly as
+ * ad_sparsify with AD_SCOPE_PER_NODE would give it.  The per-node ranking is
+ * taken once for both orders and the two exponent searches run as one
+ * two-problem search.  n_kept[2] and e_used[2] (local, global; for a batch
+ * the totals and graph 0's exponents) may be NULL.  keep_local and
+ * keep_global may each be host or device memory.  0 <= fraction <= 1.
+ * Errors: as ad_sparsify.
+ */
+ad_status ad_sparsify_local_global(ad_graph_t g, double fraction, uint8_t *keep_local, uint8_t *keep_global,
+                                   int64_t *n_kept, double *e_used);
+
+/*
  * As ad_sparsify, with caller-supplied scores score[m] (non-negative and
  * finite, e.g. precomputed distances) instead of the kept ones.  The scores
  * are compared as FP32 values.  Errors: as ad_sparsify, plus

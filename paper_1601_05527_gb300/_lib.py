@@ -72,6 +72,7 @@ _SIGS = {
     "ad_algebraic_distance_backward": (ctypes.c_int, [_VP, _VP, _VP]),
     "ad_sparsify": (ctypes.c_int, [_VP, _D, ctypes.c_int, ctypes.c_int, _VP, _PI64, _PD]),
     "ad_sparsify_scores": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, ctypes.c_int, _VP, _PI64, _PD]),
+    "ad_sparsify_local_global": (ctypes.c_int, [_VP, _D, _VP, _VP, _VP, _VP]),
     "ad_select_per_node": (ctypes.c_int, [_VP, _VP, _D, ctypes.c_int, _VP, _PI64]),
     "ad_sparsify_binned": (ctypes.c_int, [_VP, _VP, _D, _U64, _VP, _PI64, _PD]),
     "ad_binned_ranks": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
@@ -301,6 +302,17 @@ def ad_sparsify(g, fraction, mode, scope, keep_out):
     _check(load().ad_sparsify(g, float(fraction), MODES.get(mode, mode), SCOPES.get(scope, scope), k.ptr,
                               ctypes.byref(nk), ctypes.byref(e)))
     return nk.value, e.value
+
+
+def ad_sparsify_local_global(g, fraction, keep_local, keep_global):
+    """Both per-node selections (local, global) of Alg. 2 in one call;
+    returns ((kept_local, kept_global), (e_local, e_global))."""
+    kl, kg = _Arr(keep_local, np.uint8), _Arr(keep_global, np.uint8)
+    nk = (ctypes.c_int64 * 2)()
+    e = (ctypes.c_double * 2)()
+    _check(load().ad_sparsify_local_global(g, float(fraction), kl.ptr, kg.ptr, ctypes.cast(nk, _VP),
+                                           ctypes.cast(e, _VP)))
+    return (nk[0], nk[1]), (e[0], e[1])
 
 
 def ad_sparsify_scores(g, score, fraction, mode, scope, keep_out):

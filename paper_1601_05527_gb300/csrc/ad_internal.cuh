@@ -372,6 +372,8 @@ ad_status select_whole_graph(ad_graph_t g, const float *score_dev, double fracti
                              uint8_t *keep_dev, int64_t *n_kept);
 ad_status select_per_node_fit(ad_graph_t g, const float *score_dev, double fraction, ad_mode mode,
                               uint8_t *keep_dev, int64_t *n_kept, double *e_used);
+ad_status select_per_node_fit_both(ad_graph_t g, const float *score, double fraction, uint8_t *keep_local,
+                                   uint8_t *keep_global, int64_t *n_kept, double *e_used);
 ad_status select_per_node_at(ad_graph_t g, const float *score_dev, double e, ad_mode mode,
                              uint8_t *keep_dev, int64_t *n_kept);
 ad_status select_per_node_fit_ranked(ad_graph_t g, const uint32_t *rank_dev, double fraction, uint8_t *keep_dev,

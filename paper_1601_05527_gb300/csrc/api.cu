@@ -531,6 +531,44 @@ extern "C" ad_status ad_sparsify(ad_graph_t g, double fraction, ad_mode mode, ad
     return sparsify_impl(g, g->rho, fraction, mode, scope, keep_out, n_kept, e_used);
 }
 
+extern "C" ad_status ad_sparsify_local_global(ad_graph_t g, double fraction, uint8_t *keep_local,
+                                              uint8_t *keep_global, int64_t *n_kept, double *e_used) {
+    if (!g) return fail(AD_ERR_INVALID_ARG, "NULL graph");
+    if (!g->have_rho) return fail(AD_ERR_STATE, "no distances: call ad_algebraic_distance first");
+    if (!(fraction >= 0.0 && fraction <= 1.0)) return fail(AD_ERR_INVALID_ARG, "fraction must be in [0, 1]");
+    if ((!keep_local || !keep_global) && g->m > 0) return fail(AD_ERR_INVALID_ARG, "keep_local or keep_global is NULL");
+    uint8_t *out[2] = {keep_local, keep_global}, *kd[2] = {keep_local, keep_global};
+    DevBuf tmp[2];
+    ad_status st = AD_OK;
+    for (int s = 0; s < 2 && st == AD_OK; ++s)
+        if (g->m > 0 && !is_device_ptr(out[s])) {
+            st = ensure(g, tmp[s], g->m + 16);
+            kd[s] = static_cast<uint8_t *>(tmp[s].ptr);
+        }
+    int64_t kept[2] = {0, 0};
+    double e[2] = {-1.0, -1.0};
+    if (g->profiling) cudaEventRecord(g->ev0, g->stream);
+    if (st == AD_OK) st = select_per_node_fit_both(g, g->rho, fraction, kd[0], kd[1], kept, e);
+    if (st == AD_OK && g->profiling) {
+        cudaEventRecord(g->ev1, g->stream);
+        cudaEventSynchronize(g->ev1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+        g->select_ms += ms;
+        g->select_launches += 1;
+    }
+    for (int s = 0; s < 2 && st == AD_OK; ++s)
+        if (kd[s] != out[s]) st = copy_out(g, out[s], kd[s], g->m);
+    for (DevBuf &b : tmp)
+        if (b.ptr) dfree(g, b.ptr);
+    if (st != AD_OK) return st;
+    for (int s = 0; s < 2; ++s) {
+        if (n_kept) n_kept[s] = kept[s];
+        if (e_used) e_used[s] = e[s];
+    }
+    return AD_OK;
+}
+
 extern "C" ad_status ad_sparsify_scores(ad_graph_t g, const float *score, double fraction, ad_mode mode,
                                         ad_scope scope, uint8_t *keep_out, int64_t *n_kept, double *e_used) {
     if (!g) return fail(AD_ERR_INVALID_ARG, "NULL graph");

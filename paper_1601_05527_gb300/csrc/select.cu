@@ -586,10 +586,12 @@ __device__ __forceinline__ int graph_of_edge(const int64_t *goff_e, int G, int64
     return lo;
 }
 
+constexpr int kSharedFitProblems = 8;   // problems whose histograms a block keeps in shared memory
 __global__ void k_count_cand(const int4 *info, const int64_t *list, int64_t L, const int64_t *Ld, const int64_t *goff_e,
                              int G, const int32_t *T, int32_t ndc, int nc, unsigned long long *hist, uint8_t *cstar) {
-    __shared__ unsigned int h[32];
-    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __shared__ unsigned int h[kSharedFitProblems * 32];
+    const bool shared_h = G <= kSharedFitProblems;
+    for (int j = threadIdx.x; j < kSharedFitProblems * 32; j += blockDim.x) h[j] = 0;
     __syncthreads();
     if (Ld) L = *Ld;    // length of a list compacted on the device
     const int lane = threadIdx.x & 31;
@@ -613,16 +615,19 @@ __global__ void k_count_cand(const int4 *info, const int64_t *list, int64_t L, c
             cstar[t] = (uint8_t)l;
             lo = l;
         }
-        if (G == 1) {
-            // lanes with the same bin add once (few bins, so shared-memory atomics would serialise)
-            const unsigned peers = __match_any_sync(0xffffffffu, lo);
-            if (lo < 32 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[lo], (unsigned)__popc(peers));
+        if (shared_h) {
+            // lanes with the same (problem, bin) add once (few bins: shared-memory atomics would serialise)
+            const int key = lo < 32 ? gph * 32 + lo : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[key], (unsigned)__popc(peers));
         } else if (lo < 32) {
             atomicAdd(hist + (size_t)gph * 32 + lo, 1ull);
         }
     }
     __syncthreads();
-    if (G == 1 && threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(hist + threadIdx.x, (unsigned long long)h[threadIdx.x]);
+    if (shared_h)
+        for (int j = threadIdx.x; j < G * 32; j += blockDim.x)
+            if (h[j]) atomicAdd(hist + j, (unsigned long long)h[j]);
 }
 
 // undecided edges of the next pass: those whose first candidate is the chosen one
@@ -671,28 +676,81 @@ __device__ __forceinline__ int64_t fit_point(const FitState &s, int cc) {
     return cc < ni ? s.lo + step * (cc + 1) : s.hi;
 }
 
-// T of every (graph, candidate, degree class).  Tlo / Thi hold T at the ends
-// of the graph's current interval; T is monotone in e, so a class with equal
-// ends is constant inside and needs no pow.
-__global__ void k_fit_tables(const FitState *st, int G, const int64_t *ddeg, int32_t ndc, const int32_t *Tlo,
-                             const int32_t *Thi, int32_t *T, int *ambiguous) {
-    const int64_t total = (int64_t)G * kFitCand * ndc;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+// The chosen candidate of a problem from its histogram of first-kept
+// candidates: the first candidate whose cumulative count reaches K becomes the
+// new upper end, the one before it the new lower end (jsel = -1: converged).
+__device__ __forceinline__ FitState fit_choose(FitState s, const unsigned long long *h) {
+    int64_t step;
+    const int ni = fit_interior(s, step);
+    if (s.hi - s.lo <= 1) {
+        s.jsel = -1;
+        return s;
+    }
+    int64_t cum = s.base;
+    int chosen = ni;                    // the upper end always reaches K
+    for (int cc = 0; cc <= ni; ++cc) {
+        cum += (int64_t)h[cc];
+        if (cum >= s.K) { chosen = cc; break; }
+    }
+    for (int cc = 0; cc < chosen; ++cc) s.base += (int64_t)h[cc];
+    const int64_t nlo = chosen > 0 ? fit_point(s, chosen - 1) : s.lo;
+    const int64_t nhi = fit_point(s, chosen);
+    s.lo = nlo;
+    s.hi = nhi;
+    s.jsel = chosen;
+    return s;
+}
+
+// One step of the search for P problems at once, between the count of pass p
+// and the count of pass p + 1: every thread takes one (problem, candidate,
+// degree class), re-derives its problem's choice from the histogram of pass
+// p, carries T at the new interval ends (Tlo / Thi: T of the chosen point and
+// of the one before it, read from pass p's tables) and evaluates T at the
+// candidates of pass p + 1.  T is monotone in e, so a class with equal ends
+// is constant inside and needs no pow.  With first set, the state is the
+// initial one (e in [0, 1]: T = 1 and T = d at the ends) and nothing is chosen.
+// State, tables, ends and histograms are double-buffered by pass parity.
+__global__ void k_fit_advance(int P, int first, int last, const FitState *st_old, FitState *st_new,
+                              const unsigned long long *hist, unsigned long long *hist_next, const int32_t *T_cur,
+                              int32_t *T_next, const int32_t *Tlo_old, const int32_t *Thi_old, int32_t *Tlo_new,
+                              int32_t *Thi_new, const int64_t *ddeg, int32_t ndc, int64_t *next_len, int *ambiguous) {
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gtid == 0) *next_len = 0;
+    for (int64_t j = gtid; j < (int64_t)P * 32; j += (int64_t)gridDim.x * blockDim.x) hist_next[j] = 0;
+    const int64_t total = (int64_t)P * kFitCand * ndc;
+    for (int64_t idx = gtid; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
         const int q = (int)(idx % ndc);
         const int64_t kc = idx / ndc;
         const int cc = (int)(kc % kFitCand), k = (int)(kc / kFitCand);
-        const FitState s = st[k];
+        const int64_t d = ddeg[q];
+        FitState s = st_old[k];
+        int32_t tl, th;
+        if (first) {
+            tl = d > 0 ? 1 : 0;
+            th = (int32_t)d;
+        } else {
+            s = fit_choose(s, hist + (size_t)k * 32);
+            tl = Tlo_old[(size_t)k * ndc + q];
+            th = Thi_old[(size_t)k * ndc + q];
+            if (s.jsel >= 0) {
+                if (s.jsel > 0) tl = T_cur[((size_t)k * kFitCand + s.jsel - 1) * ndc + q];
+                th = T_cur[((size_t)k * kFitCand + s.jsel) * ndc + q];
+            }
+        }
+        if (cc == 0) {
+            Tlo_new[(size_t)k * ndc + q] = tl;
+            Thi_new[(size_t)k * ndc + q] = th;
+            if (q == 0) st_new[k] = s;
+        }
+        if (last) continue;
         int64_t step;
         const int ni = fit_interior(s, step);
-        const int32_t tl = Tlo[(size_t)k * ndc + q], th = Thi[(size_t)k * ndc + q];
         int32_t t;
         if (cc >= ni) {
             t = th;                              // the upper end
         } else if (tl == th) {
             t = tl;
         } else {
-            const int64_t d = ddeg[q];
             const double e = ldexp((double)(s.lo + step * (cc + 1)), -40);
             const double v = pow((double)d, e);
             const double x = v - 1e-9;
@@ -704,60 +762,7 @@ __global__ void k_fit_tables(const FitState *st, int G, const int64_t *ddeg, int
             if (c > (double)d) c = (double)d;
             t = (int32_t)c;
         }
-        T[idx] = t;
-    }
-}
-
-// T at the ends of the new interval: the tables of the chosen point and of the one before it
-__global__ void k_fit_bounds(const FitState *st, int G, int32_t ndc, const int32_t *T, int32_t *Tlo, int32_t *Thi) {
-    const int64_t total = (int64_t)G * ndc;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(idx / ndc), q = (int)(idx % ndc);
-        const int chosen = st[k].jsel;
-        if (chosen < 0) continue;
-        if (chosen > 0) Tlo[idx] = T[((size_t)k * kFitCand + chosen - 1) * ndc + q];
-        Thi[idx] = T[((size_t)k * kFitCand + chosen) * ndc + q];
-    }
-}
-
-// initial ends: e = 0 keeps one edge per node, e = 1 all of them
-__global__ void k_fit_init_bounds(int G, const int64_t *ddeg, int32_t ndc, int32_t *Tlo, int32_t *Thi) {
-    const int64_t total = (int64_t)G * ndc;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t d = ddeg[idx % ndc];
-        Tlo[idx] = d > 0 ? 1 : 0;
-        Thi[idx] = (int32_t)d;
-    }
-}
-
-// per graph: the first candidate whose count reaches K becomes the new upper end
-__global__ void k_fit_choose(FitState *st, int G, unsigned long long *hist, int64_t *next_len) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *next_len = 0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G; k += gridDim.x * blockDim.x) {
-        FitState s = st[k];
-        unsigned long long *h = hist + (size_t)k * 32;
-        int64_t step;
-        const int ni = fit_interior(s, step);
-        if (s.hi - s.lo <= 1) {
-            s.jsel = -1;
-        } else {
-            int64_t cum = s.base;
-            int chosen = ni;                    // the upper end always reaches K
-            for (int cc = 0; cc <= ni; ++cc) {
-                cum += (int64_t)h[cc];
-                if (cum >= s.K) { chosen = cc; break; }
-            }
-            for (int cc = 0; cc < chosen; ++cc) s.base += (int64_t)h[cc];
-            const int64_t nlo = chosen > 0 ? fit_point(s, chosen - 1) : s.lo;
-            const int64_t nhi = fit_point(s, chosen);
-            s.lo = nlo;
-            s.hi = nhi;
-            s.jsel = chosen;
-        }
-        for (int cc = 0; cc < 32; ++cc) h[cc] = 0;
-        st[k] = s;
+        T_next[idx] = t;
     }
 }
 
@@ -853,11 +858,11 @@ struct ad_graph_s::SelCache {
     int64_t *bpos = nullptr;        // class 8 entries: CSR position and row slot
     int32_t *bseg = nullptr;
     int64_t nb_entries = 0;
-    ad::DevBuf info, info_desc, ekey, skey, bvals, T, hist, list_a, list_b, cstar, flag, jsel, kept, st, hist3, ties,
+    ad::DevBuf info, ekey, skey, bvals, T, hist, list_a, list_b, cstar, flag, jsel, kept, st, hist3, ties,
         tie_off, ddeg, fit, fit_tb, rank2, info_other;
     int64_t *epos = nullptr;      // upper CSR entry of every edge
     bool have_ddeg = false;       // ddeg: the distinct degrees on the device
-    bool info_valid = false;      // info / info_desc hold the ranks of the handle's own distances
+    bool info_valid = false;      // info holds the ranks of the handle's own distances
     uint64_t info_version = 0;
 };
 
@@ -1060,9 +1065,8 @@ static ad_status per_node_info(ad_graph_t g, const float *score, ad_mode mode, i
     AD_TRY(sel_cache(g, &c));
     AD_TRY(rank_lists(g, c));
     const int64_t nnz = g->nnz;
-    AD_TRY(ensure(g, c->info, sizeof(int4) * (g->m + 1)));
-    AD_TRY(ensure(g, c->info_desc, sizeof(int4) * (g->m + 1)));
-    int4 *info_asc = static_cast<int4 *>(c->info.ptr), *info_desc = static_cast<int4 *>(c->info_desc.ptr);
+    AD_TRY(ensure(g, c->info, sizeof(int4) * (2 * g->m + 1)));   // local records, then the global ones
+    int4 *info_asc = static_cast<int4 *>(c->info.ptr), *info_desc = info_asc + g->m;
     *info_out = mode == AD_MODE_GLOBAL ? info_desc : info_asc;
     const bool own = score == g->rho && g->have_rho;
     if (own && c->info_valid && c->info_version == g->rho_version) return AD_OK;
@@ -1304,76 +1308,127 @@ ad_status select_local_degree(ad_graph_t g, double fraction, uint8_t *keep, int6
     return select_per_node_fit_ranked(g, out.asc, fraction, keep, n_kept, e_used);
 }
 
-static ad_status fit_search(ad_graph_t g, const int4 *info, double fraction, uint8_t *keep, int64_t *n_kept,
-                            double *e_used) {
+// The exponent search of nsets * G problems at once: problem s * G + k is
+// graph k ranked by the records at info + s * m (set s), its edges
+// [s * m + goff_e[k], s * m + goff_e[k+1]).  ev receives the fitted e of every
+// problem; *ambiguous is set when a table entry lay too close to an integer
+// for the device pow to decide it (the caller then takes the host tables).
+static ad_status fit_multi(ad_graph_t g, const int4 *info, int nsets, double fraction, std::vector<double> &ev,
+                           bool *ambiguous) {
     ad_graph_s::SelCache *c = g->sel;
-    const int G = g->G;
+    const int G = g->G, P = nsets * G;
+    const int64_t m = g->m, L0 = (int64_t)nsets * m;
     const int32_t ndc = std::max<int32_t>(g->n_deg_classes, 1);
-    if (g->m == 0 || g->n_deg_classes == 0) return select_per_node_fit_host(g, info, fraction, keep, n_kept, e_used);
-    std::vector<FitState> sh(G);
-    for (int32_t k = 0; k < G; ++k) {
-        sh[k].lo = 0;
-        sh[k].hi = (int64_t)1 << 40;
-        sh[k].K = target_count(g->eoff_h[k + 1] - g->eoff_h[k], fraction);
-        sh[k].base = 0;
-        sh[k].jsel = -1;
-        sh[k].pad = 0;
-    }
+    std::vector<FitState> sh(P);
+    std::vector<int64_t> pgoff(P + 1);
+    for (int sidx = 0; sidx < nsets; ++sidx)
+        for (int32_t k = 0; k < G; ++k) {
+            FitState &f = sh[sidx * G + k];
+            f.lo = 0;
+            f.hi = (int64_t)1 << 40;
+            f.K = target_count(g->eoff_h[k + 1] - g->eoff_h[k], fraction);
+            f.base = 0;
+            f.jsel = -1;
+            f.pad = 0;
+            pgoff[sidx * G + k] = sidx * m + g->eoff_h[k];
+        }
+    pgoff[P] = L0;
     if (!c->have_ddeg) {
         AD_TRY(ensure(g, c->ddeg, sizeof(int64_t) * ndc));
         AD_TRY(copy_in(g, c->ddeg.ptr, g->distinct_degrees.data(), sizeof(int64_t) * g->n_deg_classes));
         c->have_ddeg = true;
     }
-    AD_TRY(ensure(g, c->T, (size_t)G * kFitCand * ndc * sizeof(int32_t)));
-    AD_TRY(ensure(g, c->hist, (size_t)G * 32 * sizeof(unsigned long long)));
-    AD_TRY(ensure(g, c->cstar, (size_t)(g->m + 1)));
-    AD_TRY(ensure(g, c->list_a, sizeof(int64_t) * (g->m + 1)));
-    AD_TRY(ensure(g, c->list_b, sizeof(int64_t) * (g->m + 1)));
-    AD_TRY(ensure(g, c->fit, sizeof(FitState) * G + 4 * sizeof(int64_t)));
-    AD_TRY(ensure(g, c->fit_tb, 2 * sizeof(int32_t) * (size_t)G * ndc));
-    int32_t *Tlo = static_cast<int32_t *>(c->fit_tb.ptr), *Thi = Tlo + (size_t)G * ndc;
-    FitState *st = static_cast<FitState *>(c->fit.ptr);
-    int64_t *len = reinterpret_cast<int64_t *>(st + G);        // [0], [1]: list lengths; [2]: ambiguity flag
+    const size_t tsz = (size_t)P * kFitCand * ndc, bsz = (size_t)P * ndc;
+    AD_TRY(ensure(g, c->T, 2 * tsz * sizeof(int32_t)));
+    AD_TRY(ensure(g, c->hist, (size_t)2 * P * 32 * sizeof(unsigned long long)));
+    AD_TRY(ensure(g, c->cstar, (size_t)(L0 + 1)));
+    AD_TRY(ensure(g, c->list_a, sizeof(int64_t) * (L0 + 1)));
+    AD_TRY(ensure(g, c->list_b, sizeof(int64_t) * (L0 + 1)));
+    AD_TRY(ensure(g, c->fit, 3 * sizeof(FitState) * P + 4 * sizeof(int64_t) + sizeof(int64_t) * (P + 1)));
+    AD_TRY(ensure(g, c->fit_tb, 4 * bsz * sizeof(int32_t)));
+    FitState *stb = static_cast<FitState *>(c->fit.ptr);          // [0], [1]: by pass parity; [2]: initial
+    FitState *st[2] = {stb, stb + P};
+    int64_t *len = reinterpret_cast<int64_t *>(stb + 3 * P);      // [0], [1]: list lengths; [2]: ambiguity flag
     int *amb = reinterpret_cast<int *>(len + 2);
-    int32_t *T = static_cast<int32_t *>(c->T.ptr);
-    unsigned long long *hist = static_cast<unsigned long long *>(c->hist.ptr);
+    int64_t *goff = len + 4;
+    int32_t *tb = static_cast<int32_t *>(c->fit_tb.ptr);
+    int32_t *Tlo[2] = {tb, tb + bsz}, *Thi[2] = {tb + 2 * bsz, tb + 3 * bsz};
+    int32_t *T[2] = {static_cast<int32_t *>(c->T.ptr), static_cast<int32_t *>(c->T.ptr) + tsz};
+    unsigned long long *hist[2] = {static_cast<unsigned long long *>(c->hist.ptr),
+                                   static_cast<unsigned long long *>(c->hist.ptr) + (size_t)P * 32};
     uint8_t *cstar = static_cast<uint8_t *>(c->cstar.ptr);
     int64_t *lists[2] = {static_cast<int64_t *>(c->list_a.ptr), static_cast<int64_t *>(c->list_b.ptr)};
-    AD_TRY(copy_in(g, st, sh.data(), sizeof(FitState) * G));
+    const int64_t *ddeg = static_cast<const int64_t *>(c->ddeg.ptr);
+    AD_TRY(copy_in(g, stb + 2 * P, sh.data(), sizeof(FitState) * P));
+    AD_TRY(copy_in(g, goff, pgoff.data(), sizeof(int64_t) * (P + 1)));
     AD_CUDA_TRY(cudaMemsetAsync(len, 0, 4 * sizeof(int64_t), g->stream));
-    AD_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)G * 32 * sizeof(unsigned long long), g->stream));
     const int big = g->num_sms * 16;
-    const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)G * kFitCand * ndc + 255) / 256, big));
-    const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, big));
-    const int gblocks = (G + 255) / 256;
-    const int bblocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)G * ndc + 255) / 256, big));
-    AD_LAUNCH(k_fit_init_bounds, bblocks, 256, 0, g->stream, G, static_cast<const int64_t *>(c->ddeg.ptr), ndc, Tlo,
-              Thi);
+    const int ablocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)tsz + 255) / 256, big));
+    const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((L0 + 255) / 256, big));
+    // initial state, ends and the tables of pass 0
+    AD_LAUNCH(k_fit_advance, ablocks, 256, 0, g->stream, P, 1, 0, stb + 2 * P, st[0], hist[1], hist[0], T[1], T[0],
+              Tlo[1], Thi[1], Tlo[0], Thi[0], ddeg, ndc, len + 1, amb);
     for (int pass = 0; pass < kFitPasses; ++pass) {
-        const int64_t *lin = pass == 0 ? nullptr : lists[pass & 1];
-        const int64_t *lin_len = pass == 0 ? nullptr : len + (pass & 1);
-        int64_t *lout = lists[(pass + 1) & 1], *lout_len = len + ((pass + 1) & 1);
-        AD_LAUNCH(k_fit_tables, tblocks, 256, 0, g->stream, st, G, static_cast<const int64_t *>(c->ddeg.ptr), ndc, Tlo,
-                  Thi, T, amb);
-        AD_LAUNCH(k_count_cand, cblocks, 256, 0, g->stream, info, lin, g->m, lin_len, g->goff_e, G, T, ndc, kFitCand,
-                  hist, cstar);
-        AD_LAUNCH(k_fit_choose, gblocks, 256, 0, g->stream, st, G, hist, lout_len);
-        if (pass + 1 < kFitPasses) AD_LAUNCH(k_fit_bounds, bblocks, 256, 0, g->stream, st, G, ndc, T, Tlo, Thi);
-        if (pass + 1 < kFitPasses)
-            AD_LAUNCH(k_fit_compact, cblocks, 256, 0, g->stream, lin, g->m, lin_len, cstar, g->goff_e, G, st, lout,
-                      lout_len);
+        const int a = pass & 1, b = a ^ 1;
+        const bool last = pass + 1 == kFitPasses;
+        AD_LAUNCH(k_count_cand, cblocks, 256, 0, g->stream, info, pass == 0 ? nullptr : lists[a], L0,
+                  pass == 0 ? nullptr : len + a, goff, P, T[a], ndc, kFitCand, hist[a], cstar);
+        AD_LAUNCH(k_fit_advance, ablocks, 256, 0, g->stream, P, 0, last ? 1 : 0, st[a], st[b], hist[a], hist[b], T[a],
+                  T[b], Tlo[a], Thi[a], Tlo[b], Thi[b], ddeg, ndc, len + b, amb);
+        if (!last)
+            AD_LAUNCH(k_fit_compact, cblocks, 256, 0, g->stream, pass == 0 ? nullptr : lists[a], L0,
+                      pass == 0 ? nullptr : len + a, cstar, goff, P, st[b], lists[b], len + b);
     }
-    AD_TRY(copy_out(g, sh.data(), st, sizeof(FitState) * G));
+    AD_TRY(copy_out(g, sh.data(), st[kFitPasses & 1], sizeof(FitState) * P));
     int amb_h = 0;
     AD_TRY(copy_out(g, &amb_h, amb, sizeof(int)));
-    if (amb_h) return select_per_node_fit_host(g, info, fraction, keep, n_kept, e_used);
-    std::vector<double> ev(G);
-    for (int32_t k = 0; k < G; ++k) {
+    *ambiguous = amb_h != 0;
+    ev.assign(P, -1.0);
+    if (*ambiguous) return AD_OK;
+    for (int k = 0; k < P; ++k) {
         if (sh[k].hi - sh[k].lo > 1) return fail(AD_ERR_CUDA, "exponent search did not converge");
         ev[k] = std::ldexp((double)sh[k].hi, -40);
     }
+    return AD_OK;
+}
+
+static ad_status fit_search(ad_graph_t g, const int4 *info, double fraction, uint8_t *keep, int64_t *n_kept,
+                            double *e_used) {
+    if (g->m == 0 || g->n_deg_classes == 0) return select_per_node_fit_host(g, info, fraction, keep, n_kept, e_used);
+    std::vector<double> ev;
+    bool amb = false;
+    AD_TRY(fit_multi(g, info, 1, fraction, ev, &amb));
+    if (amb) return select_per_node_fit_host(g, info, fraction, keep, n_kept, e_used);
     AD_TRY(keep_at(g, info, ev, keep, n_kept));
-    if (e_used) *e_used = G > 0 ? ev[0] : -1.0;
+    if (e_used) *e_used = g->G > 0 ? ev[0] : -1.0;
+    return AD_OK;
+}
+
+// Alg. 2 in both orders (local: smallest rho first; global: largest first) on
+// the same scores: one ranking pass, one two-set exponent search.
+ad_status select_per_node_fit_both(ad_graph_t g, const float *score, double fraction, uint8_t *keep_local,
+                                   uint8_t *keep_global, int64_t *n_kept, double *e_used) {
+    int4 *info = nullptr;
+    AD_TRY(per_node_info(g, score, AD_MODE_LOCAL, &info));   // the global records follow at info + m
+    uint8_t *keep[2] = {keep_local, keep_global};
+    if (g->m == 0 || g->n_deg_classes == 0) {
+        for (int sidx = 0; sidx < 2; ++sidx)
+            AD_TRY(select_per_node_fit_host(g, info + sidx * g->m, fraction, keep[sidx], n_kept + sidx, e_used + sidx));
+        return AD_OK;
+    }
+    std::vector<double> ev;
+    bool amb = false;
+    AD_TRY(fit_multi(g, info, 2, fraction, ev, &amb));
+    for (int sidx = 0; sidx < 2; ++sidx) {
+        const int4 *inf = info + sidx * g->m;
+        if (amb) {
+            AD_TRY(select_per_node_fit_host(g, inf, fraction, keep[sidx], n_kept + sidx, e_used + sidx));
+            continue;
+        }
+        std::vector<double> es(ev.begin() + sidx * g->G, ev.begin() + (sidx + 1) * g->G);
+        AD_TRY(keep_at(g, inf, es, keep[sidx], n_kept + sidx));
+        e_used[sidx] = g->G > 0 ? es[0] : -1.0;
+    }
     return AD_OK;
 }
 

@@ -251,3 +251,41 @@ def test_cached_ranks_follow_the_distances():
     check_own("global")
     check_own("local")
     L.ad_graph_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["rmat13", "hubs", "batch"])
+def test_local_and_global_in_one_call(name):
+    """ad_sparsify_local_global (one ranking, one two-problem exponent search)
+    against the oracle's per-node selections in each order, on the GPU's own
+    distances: kept sets, counts and exponents exact."""
+    import torch
+    L = lib()
+    if name == "batch":
+        graphs, voff, big = make_batch([1000, 2345, 1500, 5000, 1200], seed=9)
+        h = L.ad_graph_create_batched(voff, big.n, big.row_ptr, big.col, None)
+        eoff = L.ad_graph_edge_offsets(h)
+        g = big
+    else:
+        g = graphgen.rmat(13, 16, seed=8) if name == "rmat13" else hub_graph()
+        graphs, eoff = [g], [0, g.m]
+        h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
+    try:
+        rho = np.zeros(g.m, np.float32)
+        L.ad_algebraic_distance(h, 16, 10, 0.5, 3, 0, "fp32", 0, rho)
+        for f in (0.1, 0.3, 0.75):
+            kl = np.zeros(g.m, np.uint8)
+            kg = torch.zeros(g.m, dtype=torch.uint8, device="cuda")
+            (nl, ng), (el, eg) = L.ad_sparsify_local_global(h, f, kl, kg)
+            kg = kg.cpu().numpy()
+            tot = [0, 0]
+            for k, gg in enumerate(graphs):
+                part = rho[eoff[k]:eoff[k + 1]].astype(np.float64)
+                for j, (mode, keep) in enumerate((("local", kl), ("global", kg))):
+                    ref, rk, re_ = oracle.sparsify(gg.row_ptr, gg.col, part, mode, "per_node", f)
+                    np.testing.assert_array_equal(keep[eoff[k]:eoff[k + 1]], ref)
+                    tot[j] += rk
+                    if k == 0:
+                        assert (el, eg)[j] == re_
+            assert (nl, ng) == tuple(tot)
+    finally:
+        L.ad_graph_destroy(h)
