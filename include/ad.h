@@ -87,8 +87,9 @@ typedef enum {
 
 /* ad_algebraic_distance flags */
 #define AD_DIST_NORMALIZE 0x1           /* score rho * sqrt(D_i D_j): the optional last line of Alg. 1 */
-#define AD_DIST_KEEP_STATE 0x2          /* keep sqrt(k) checkpoints for ad_algebraic_distance_backward */
+#define AD_DIST_KEEP_STATE 0x2          /* keep the iterates ad_algebraic_distance_backward needs */
 #define AD_DIST_PERSISTENT 0x4          /* init, all sweeps and distances in one persistent launch (single graphs) */
+#define AD_DIST_SQRT_CHECKPOINTS 0x8    /* with AD_DIST_KEEP_STATE: only every ceil(sqrt k)-th iterate */
 
 typedef struct ad_graph_s *ad_graph_t;
 typedef struct ad_ml_s *ad_ml_t;
@@ -225,8 +226,11 @@ ad_status ad_graph_set_edge_weights(ad_graph_t g, const float *w_edge);
  * storage: FP32 or BF16 storage of the vectors between sweeps (FP32
  * accumulation either way).  rho_out[m] may be NULL; the scores are kept in
  * the handle for ad_sparsify either way.  With AD_DIST_KEEP_STATE the
- * iterates needed by ad_algebraic_distance_backward are kept (ceil(sqrt k)
- * checkpoints).  With AD_DIST_PERSISTENT a single graph (not a batch) is
+ * iterates needed by ad_algebraic_distance_backward are kept: all k + 1 of
+ * them when they take at most half of the device's free memory (the backward
+ * then recomputes none), otherwise -- or with AD_DIST_SQRT_CHECKPOINTS --
+ * every ceil(sqrt k)-th one, from which the backward recomputes the others.
+ * The gradient is bit-identical either way (the sweep is deterministic).  With AD_DIST_PERSISTENT a single graph (not a batch) is
  * computed in one persistent cooperative launch: init, the k sweeps separated
  * by grid-wide barriers (each rescale needs the min/max over all vertices),
  * then the distances, with bit-identical results; a barrier waits at most a

@@ -28,6 +28,7 @@ AD_CREATE_SKIP_VALIDATION = 0x1
 AD_DIST_NORMALIZE = 0x1
 AD_DIST_KEEP_STATE = 0x2
 AD_DIST_PERSISTENT = 0x4
+AD_DIST_SQRT_CHECKPOINTS = 0x8
 
 MODES = {"local": AD_MODE_LOCAL, "global": AD_MODE_GLOBAL}
 SCOPES = {"per_node": AD_SCOPE_PER_NODE, "whole_graph": AD_SCOPE_WHOLE_GRAPH}

@@ -402,7 +402,7 @@ ad_status create_like(ad_graph_t parent, int64_t n, const int64_t *rp_dev, const
 
 // reverse mode (grad.cu)
 ad_status algebraic_distance_keep(ad_graph_t g, int32_t R, int32_t k, double omega, uint64_t seed,
-                                  uint32_t stream_id, float *rho_dev);
+                                  uint32_t stream_id, float *rho_dev, bool sqrt_checkpoints);
 void free_saved(ad_graph_t g);
 
 // host-side exact degree target of Alg. 2 (same formula as the documented reading)

@@ -408,14 +408,15 @@ extern "C" ad_status ad_algebraic_distance(ad_graph_t g, int32_t R, int32_t k, d
     if (k < 0) return fail(AD_ERR_INVALID_ARG, "k must be >= 0");
     if (!(omega > 0.0 && omega <= 1.0)) return fail(AD_ERR_INVALID_ARG, "omega must be in (0, 1]");
     if (storage < AD_STORAGE_FP32 || storage > AD_STORAGE_Q16) return fail(AD_ERR_INVALID_ARG, "bad storage");
-    if (flags & ~(AD_DIST_NORMALIZE | AD_DIST_KEEP_STATE | AD_DIST_PERSISTENT))
+    if (flags & ~(AD_DIST_NORMALIZE | AD_DIST_KEEP_STATE | AD_DIST_PERSISTENT | AD_DIST_SQRT_CHECKPOINTS))
         return fail(AD_ERR_INVALID_ARG, "unknown flags");
     if ((flags & AD_DIST_KEEP_STATE) && (storage != AD_STORAGE_FP32 || (flags & AD_DIST_NORMALIZE)))
         return fail(AD_ERR_INVALID_ARG, "kept state needs FP32 storage and no normalisation");
     if (!g->rho) AD_TRY(dalloc_t(g, g->m + 1, &g->rho));
     g->have_rho = false;
     g->rho_version++;
-    if (flags & AD_DIST_KEEP_STATE) AD_TRY(algebraic_distance_keep(g, R, k, omega, seed, stream_id, g->rho));
+    if (flags & AD_DIST_KEEP_STATE)
+        AD_TRY(algebraic_distance_keep(g, R, k, omega, seed, stream_id, g->rho, (flags & AD_DIST_SQRT_CHECKPOINTS) != 0));
     else AD_TRY(distance_replayed(g, R, k, omega, seed, stream_id, storage, flags));
     g->have_rho = true;
     g->rho_version++;

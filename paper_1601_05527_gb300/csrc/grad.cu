@@ -32,9 +32,10 @@
 
 struct ad_graph_s::Saved {
     int32_t R = 0, k = 0, c = 1;
+    bool all = false;             // ckpt holds every iterate s_0 .. s_k (c = 1)
     double omega = 0.5;
     int32_t stride = 0, nchunks = 0, lpr = 1, cpl = 1;
-    std::vector<void *> ckpt;     // stored vectors after sweep 0, c, 2c, ...
+    std::vector<void *> ckpt;     // stored vectors after sweep 0, c, 2c, ... (all: after every sweep)
     uint32_t *mm = nullptr;       // [2][k][stride] min then max slots of every sweep
     float *rho = nullptr;         // forward distances
 };
@@ -51,7 +52,7 @@ void free_saved(ad_graph_t g) {
 }
 
 ad_status algebraic_distance_keep(ad_graph_t g, int32_t R, int32_t k, double omega, uint64_t seed, uint32_t stream_id,
-                                  float *rho_dev) {
+                                  float *rho_dev, bool sqrt_checkpoints) {
     if (g->G != 1) return fail(AD_ERR_INVALID_ARG, "the reverse mode takes a single graph, not a batch");
     free_saved(g);
     auto *sv = new ad_graph_s::Saved();
@@ -59,9 +60,6 @@ ad_status algebraic_distance_keep(ad_graph_t g, int32_t R, int32_t k, double ome
     sv->R = R;
     sv->k = k;
     sv->omega = omega;
-    int c = 1;
-    while ((int64_t)c * c < k) ++c;
-    sv->c = c;
     const int V = 4;
     const int nch = (R + V - 1) / V;
     int p2 = 1;
@@ -71,9 +69,19 @@ ad_status algebraic_distance_keep(ad_graph_t g, int32_t R, int32_t k, double ome
     sv->cpl = p2 / sv->lpr;
     sv->stride = p2 * V;
     const size_t xbytes = ((size_t)g->n + 1) * sv->stride * sizeof(float);
+    // every iterate s_0 .. s_k when they fit in half of the free memory (the
+    // backward then recomputes nothing), else s_0, s_c, s_2c, ... with c = ceil(sqrt k)
+    size_t free_b = 0, total_b = 0;
+    const bool all = !sqrt_checkpoints && k > 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+                     (size_t)(k + 1) * xbytes <= free_b / 2;
+    int c = 1;
+    if (!all)
+        while ((int64_t)c * c < k) ++c;
+    sv->c = c;
+    sv->all = all;
     KeepSpec ks;
     ks.every = c;
-    const int nck = k > 0 ? (k + c - 1) / c : 1;
+    const int nck = all ? k + 1 : k > 0 ? (k + c - 1) / c : 1;
     for (int j = 0; j < nck; ++j) {
         void *p = nullptr;
         AD_TRY(dalloc(g, xbytes, &p));
@@ -168,7 +176,10 @@ __device__ __forceinline__ void bw_gather(const BwArgs &a, int64_t row, int64_t 
 // before any is used, and the per-entry dots are summed over the group's lanes
 // together (group_sums)
 #ifndef AD_BW_UB
-#define AD_BW_UB 4
+#define AD_BW_UB 8            // neighbours in flight per group (measured at R-MAT 22: 8 with 3 CTAs per SM fastest)
+#endif
+#ifndef AD_BW_GPF
+#define AD_BW_GPF 1
 #endif
 constexpr int kBwUB = AD_BW_UB;
 template <int LPR, int CPL>
@@ -176,6 +187,17 @@ __device__ __forceinline__ void bw_gather_adjoint(const BwArgs &a, int64_t p0, i
                                                   int gl, unsigned gmask, const float (&v)[CPL * 4],
                                                   float (&acc_a)[CPL * 4], float (&acc_b)[CPL * 4]) {
     constexpr int UB = kBwUB;
+    constexpr int NH = UB / LPR > 0 ? UB / LPR : 1;
+    constexpr int WS = LPR > UB ? LPR / UB : 1;   // lanes per entry that hold the same dot
+    const bool writer = gl % WS == 0;
+    // the entries whose dots this lane will hold after group_sums
+    int which = 0;
+#pragma unroll
+    for (int o = LPR / 2, c = UB; o >= 1; o >>= 1)
+        if (c > 1) {
+            if (gl & o) which += c / 2;
+            c >>= 1;
+        }
     for (int64_t pb = p0 + first; pb < p1; pb += (int64_t)gstride * UB) {
         int32_t jn[UB];
         float wt[UB];
@@ -186,6 +208,15 @@ __device__ __forceinline__ void bw_gather_adjoint(const BwArgs &a, int64_t p0, i
             jn[u] = ok ? __ldg(a.col + p) : 0;
             wt[u] = ok ? (a.w ? __ldg(a.w + p) : 1.f) : 0.f;
         }
+#if AD_BW_GPF
+        // the accumulators of those entries, loaded with the rows so that their latency overlaps
+        double gold[NH];
+#pragma unroll
+        for (int i = 0; i < NH; ++i) {
+            const int64_t p = pb + (int64_t)(which + i) * gstride;
+            gold[i] = (writer && p < p1) ? __ldcg(a.G + p) : 0.0;
+        }
+#endif
         float4 uu[UB][CPL], ss[UB][CPL];
 #pragma unroll
         for (int u = 0; u < UB; ++u)
@@ -214,14 +245,16 @@ __device__ __forceinline__ void bw_gather_adjoint(const BwArgs &a, int64_t p0, i
                 }
             }
         }
-        int which = 0;
-        group_sums<LPR, UB>(dot, gl, gmask, which);
-        constexpr int NH = UB / LPR > 0 ? UB / LPR : 1;
-        const bool writer = (LPR <= UB) || (gl % (LPR / UB) == 0);
+        int w2 = 0;
+        group_sums<LPR, UB>(dot, gl, gmask, w2);
 #pragma unroll
         for (int i = 0; i < NH; ++i) {
             const int64_t p = pb + (int64_t)(which + i) * gstride;
+#if AD_BW_GPF
+            if (writer && p < p1) a.G[p] = gold[i] + (double)dot[i];
+#else
             if (writer && p < p1) a.G[p] += (double)dot[i];
+#endif
         }
     }
 }
@@ -286,7 +319,7 @@ __device__ __forceinline__ void bw_own(const BwArgs &a, int64_t row, int gl, flo
 }
 
 #ifndef AD_BW_MINB
-#define AD_BW_MINB 4          // 4 CTAs per SM (measured: 21% faster than the unbounded register count)
+#define AD_BW_MINB 3          // CTAs per SM (measured: 3 with 8 neighbours in flight beat 4-6 with 2 or 4)
 #endif
 template <int LPR, int CPL>
 __global__ void __launch_bounds__(256, AD_BW_MINB) k_bw(BwArgs a) {
@@ -372,30 +405,9 @@ __global__ void __launch_bounds__(256, AD_BW_MINB) k_bw(BwArgs a) {
     }
 }
 
-// lowest-index argmin / argmax of each vector of the stored iterate (active
-// rows); one thread per 16-byte chunk, stride = 1 << sshift
-__global__ void k_bw_argext(const float *S, const int64_t *rp, int64_t n, int32_t sshift, int32_t R,
-                            const uint32_t *mn, const uint32_t *mx, unsigned long long *amin, unsigned long long *amax) {
-    const int qshift = sshift - 2, qmask = (1 << qshift) - 1;
-    const int64_t total = n << qshift;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t >> qshift;
-        const int q = (int)(t & qmask);
-        if (4 * q >= R || rp[i + 1] == rp[i]) continue;
-        const float4 v4 = __ldg(reinterpret_cast<const float4 *>(S) + t);
-        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int r = 4 * q + e;
-            if (r >= R) break;
-            if (v[e] == ord2f(mn[r])) atomicMin(amin + r, (unsigned long long)i);
-            if (v[e] == ord2f(mx[r])) atomicMin(amax + r, (unsigned long long)i);
-        }
-    }
-}
-
 // per-block partial sums of A = sum xbar (x - 1/2) and B = sum xbar (x + 1/2),
-// x = a (s - lo) - 1/2.  Products in FP32 (FP64 runs on a very narrow pipe on
+// x = a (s - lo) - 1/2, and the lowest-index argmin / argmax of each vector
+// of the stored iterate (active rows).  Products in FP32 (FP64 runs on a very narrow pipe on
 // this part), each thread's running sums compensated (Kahan), the threads'
 // sums combined in FP64.  B = A + sum xbar.
 constexpr int kRedBlocks = 1216;      // 8 per SM: the per-thread sums are latency bound
@@ -407,7 +419,8 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 }
 
 __global__ void k_bw_partial(const float *xbar, const float *S, const int64_t *rp, int64_t n, int32_t stride, int32_t R,
-                             const uint32_t *mn, const float *a_t, double *partA, double *partB) {
+                             const uint32_t *mn, const uint32_t *mx, const float *a_t, double *partA, double *partB,
+                             unsigned long long *amin, unsigned long long *amax) {
     __shared__ double sA[256], sB[256];
     // thread layout: r = threadIdx.x % R, rows strided over the block's R-wide slices
     const int Rp = R;
@@ -416,12 +429,16 @@ __global__ void k_bw_partial(const float *xbar, const float *S, const int64_t *r
     const int sub = threadIdx.x / Rp;
     float accA = 0.f, cA = 0.f, accX = 0.f, cX = 0.f;
     if (sub < lanes_per && threadIdx.x < lanes_per * Rp) {
-        const float lo = ord2f(mn[r]);
+        const float lo = ord2f(mn[r]), hi = ord2f(mx[r]);
         const float ar = a_t[r];
         for (int64_t i = (int64_t)blockIdx.x * lanes_per + sub; i < n; i += (int64_t)gridDim.x * lanes_per) {
             if (rp[i + 1] == rp[i]) continue;
             const float xb = xbar[i * stride + r];
-            const float xv = ar * (S[i * stride + r] - lo) - 0.5f;
+            const float sv = S[i * stride + r];
+            // the lowest-index argmin / argmax of vector r (the rescale's sub-gradient points)
+            if (sv == lo) atomicMin(amin + r, (unsigned long long)i);
+            if (sv == hi) atomicMin(amax + r, (unsigned long long)i);
+            const float xv = ar * (sv - lo) - 0.5f;
             kahan_add(accA, cA, xb * (xv - 0.5f));
             kahan_add(accX, cX, xb);
         }
@@ -437,13 +454,25 @@ __global__ void k_bw_partial(const float *xbar, const float *S, const int64_t *r
     }
 }
 
+// one warp per vector r: the lanes sum every 32nd block's partial, then a butterfly
 __global__ void k_bw_reduce(const double *partA, const double *partB, int nblocks, int32_t R, double *A, double *B) {
-    const int r = threadIdx.x;
-    if (r >= R) return;
-    double tA = 0.0, tB = 0.0;
-    for (int b = 0; b < nblocks; ++b) { tA += partA[(int64_t)b * R + r]; tB += partB[(int64_t)b * R + r]; }
-    A[r] = tA;
-    B[r] = tB;
+    const int lane = threadIdx.x & 31;
+    for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
+        double tA = 0.0, tB = 0.0;
+        for (int b = lane; b < nblocks; b += 32) {
+            tA += partA[(int64_t)b * R + r];
+            tB += partB[(int64_t)b * R + r];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tA += __shfl_xor_sync(0xffffffffu, tA, o);
+            tB += __shfl_xor_sync(0xffffffffu, tB, o);
+        }
+        if (lane == 0) {
+            A[r] = tA;
+            B[r] = tB;
+        }
+    }
 }
 
 // ybar = a xbar (+ a A at the argmin, - a B at the argmax); U = D^-1 ybar.
@@ -530,11 +559,6 @@ static void fill_bw_plan(BwArgs &a, const RowPlan &p) {
     a.n_tasks = p.tasks();
 }
 
-static inline int nb(int64_t n, int per = 256) {
-    const int64_t b = (n + per - 1) / per;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
-}
-
 ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
     auto *sv = g->saved;
     const int32_t R = sv->R, k = sv->k, c = sv->c, stride = sv->stride;
@@ -544,7 +568,8 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
     AD_TRY(get_row_plan(g, 32 / sv->lpr, false, &plan));
     // buffers
     std::vector<float *> seg(c + 1, nullptr);
-    for (int u = 1; u <= c; ++u) AD_TRY(dalloc_t(g, (n + 1) * stride, &seg[u]));
+    if (!sv->all)   // (with every iterate kept, seg points into the kept iterates)
+        for (int u = 1; u <= c; ++u) AD_TRY(dalloc_t(g, (n + 1) * stride, &seg[u]));
     float *xbar = nullptr, *xbar2 = nullptr, *ybar = nullptr, *U = nullptr, *part = nullptr;
     float *a_t = nullptr, *a_p = nullptr, *a_k = nullptr;   // scales of sweep t, t - 1 and k
     double *G = nullptr, *C = nullptr, *partA = nullptr, *partB = nullptr, *A = nullptr, *B = nullptr;
@@ -595,6 +620,10 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
         seg[0] = static_cast<float *>(sv->ckpt[j]);
         for (int u = 1; u <= len; ++u) {
             const int t = t0 + u;   // produce s_t from s_{t-1}
+            if (sv->all) {          // kept by the forward: the same values the sweep would give
+                seg[u] = static_cast<float *>(sv->ckpt[t]);
+                continue;
+            }
             AD_CUDA_TRY(cudaMemsetAsync(scratch_mm, 0xff, stride * sizeof(uint32_t), g->stream));
             AD_CUDA_TRY(cudaMemsetAsync(scratch_mm + stride, 0, stride * sizeof(uint32_t), g->stream));
             AD_TRY(sweep_step(g, AD_STORAGE_FP32, R, sv->omega, seg[u - 1], seg[u], t >= 2 ? slot_min(t - 1) : nullptr,
@@ -616,11 +645,9 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
             AD_LAUNCH(k_scale_from_mm, 1, 256, 0, g->stream, slot_min(t), slot_max(t), stride, a_t);
             AD_CUDA_TRY(cudaMemsetAsync(amin, 0xff, stride * sizeof(unsigned long long), g->stream));
             AD_CUDA_TRY(cudaMemsetAsync(amax, 0xff, stride * sizeof(unsigned long long), g->stream));
-            AD_LAUNCH(k_bw_argext, g->num_sms * 16, 256, 0, g->stream, St, g->rp, n, sshift, R, slot_min(t),
-                      slot_max(t), amin, amax);
-            AD_LAUNCH(k_bw_partial, kRedBlocks, 256, 0, g->stream, xbar, St, g->rp, n, stride, R, slot_min(t), a_t, partA,
-                      partB);
-            AD_LAUNCH(k_bw_reduce, 1, 256, 0, g->stream, partA, partB, kRedBlocks, R, A, B);
+            AD_LAUNCH(k_bw_partial, kRedBlocks, 256, 0, g->stream, xbar, St, g->rp, n, stride, R, slot_min(t),
+                      slot_max(t), a_t, partA, partB, amin, amax);
+            AD_LAUNCH(k_bw_reduce, 1, 1024, 0, g->stream, partA, partB, kRedBlocks, R, A, B);
             AD_LAUNCH(k_bw_ybar, g->num_sms * 16, 256, 0, g->stream, xbar, g->rp, g->Dinv, n, sshift, R, a_t, A, B, amin,
                       amax, ybar, U);
             // sweep adjoint + weight terms
@@ -642,7 +669,8 @@ ad_status backward(ad_graph_t g, const float *rhobar_dev, float *wbar_dev) {
     AD_LAUNCH(k_edge_grad, g->num_sms * 16, 256, 0, g->stream, g->rp, g->col, g->upos, g->eoff, g->mirror, g->erow, g->D,
               nnz, G, C, sv->omega, wbar_dev);
     AD_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    for (int u = 1; u <= c; ++u) dfree(g, seg[u]);
+    if (!sv->all)
+        for (int u = 1; u <= c; ++u) dfree(g, seg[u]);
     for (void *p : {(void *)xbar, (void *)xbar2, (void *)ybar, (void *)U, (void *)part, (void *)G, (void *)C,
                     (void *)partA, (void *)partB, (void *)A, (void *)B, (void *)amin, (void *)amax, (void *)a_t, (void *)a_p, (void *)a_k,
                     (void *)scratch_mm})

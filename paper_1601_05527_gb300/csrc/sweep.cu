@@ -278,9 +278,13 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
     a.ac = static_cast<float *>(g->ac.ptr);
 
     void *xin = g->x0.ptr, *xout = g->x1.ptr;
+    // every iterate kept: the sweeps read and write the kept buffers directly
+    const bool direct = keep && keep->every == 1 && keep->ckpt.size() == (size_t)k + 1;
+    if (direct) xin = keep->ckpt[0];
     const size_t smem = 2 * 8 * (size_t)cf.stride * sizeof(float);
     fill_plan(a, *sp);
     for (int32_t t = 0; t < k; ++t) {
+        if (direct) xout = keep->ckpt[t + 1];
         a.x_in = xin; a.x_out = xout;
         const size_t slot = (size_t)g->G * cf.stride;
         a.mm_prev_min = t > 0 ? mm_min + (size_t)(t - 1) * slot : nullptr;
@@ -290,7 +294,7 @@ ad_status algebraic_distance(ad_graph_t g, int32_t R, int32_t k, double omega, u
         ev_begin(g);
         AD_TRY(dispatch_storage(g, storage, cf, true, a, smem));
         ev_end(g, g->sweep_ms, g->sweep_launches);
-        if (keep && (t + 1) % keep->every == 0 && (size_t)((t + 1) / keep->every) < keep->ckpt.size())
+        if (keep && !direct && (t + 1) % keep->every == 0 && (size_t)((t + 1) / keep->every) < keep->ckpt.size())
             AD_CUDA_TRY(cudaMemcpyAsync(keep->ckpt[(t + 1) / keep->every], xout, (size_t)g->n * cf.stride * esz,
                                         cudaMemcpyDeviceToDevice, g->stream));
         void *tmp = xin; xin = xout; xout = tmp;

@@ -23,17 +23,31 @@ def grad_error(gpu, ref):
     return float(np.max(np.abs(gpu.astype(np.float64) - ref)) / scale)
 
 
-def gpu_loss_grad(g, S, R, k, omega, seed):
+def gpu_loss_grad(g, S, R, k, omega, seed, extra_flags=0):
     L = lib()
     h = L.ad_graph_create(g.n, g.row_ptr, g.col, g.weight)
     rho = np.zeros(g.m, np.float32)
-    L.ad_algebraic_distance(h, R, k, omega, seed, 0, "fp32", L.AD_DIST_KEEP_STATE, rho)
+    L.ad_algebraic_distance(h, R, k, omega, seed, 0, "fp32", L.AD_DIST_KEEP_STATE | extra_flags, rho)
     rb = np.zeros(g.m, np.float32)
     rb[S] = 2.0 * rho[S]
     wb = np.zeros(g.m, np.float32)
     L.ad_algebraic_distance_backward(h, rb, wb)
     L.ad_graph_destroy(h)
     return float((rho[S].astype(np.float64) ** 2).sum()), wb
+
+
+@pytest.mark.parametrize("k", [1, 9, 12])
+def test_every_iterate_kept_equals_sqrt_checkpoints(k):
+    """The backward either uses every kept iterate or recomputes them from
+    ceil(sqrt k) checkpoints; the sweep is deterministic, so the two gradients
+    must be identical bit for bit (k = 9: whole segments, k = 12: a short last one)."""
+    L = lib()
+    g = weighted(graphgen.rmat(11, 16, seed=4), 3)
+    S = graphgen.random_edge_subset(g.m, 0.05, seed=2)
+    la, wa = gpu_loss_grad(g, S, 16, k, 0.5, 7)
+    lb, wb = gpu_loss_grad(g, S, 16, k, 0.5, 7, L.AD_DIST_SQRT_CHECKPOINTS)
+    assert la == lb
+    np.testing.assert_array_equal(wa, wb)
 
 
 @pytest.mark.parametrize("name,make,R,k", [
