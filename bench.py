@@ -468,14 +468,15 @@ def workload_grid64(L, dev, stream, steps, warmup):
             "note": "latency-bound: microseconds per call, repeated calls replay a recorded CUDA graph"}
 
 
-def workload_ws512(L, dev, stream, steps, warmup, storage="bf16"):
+def workload_ws512(L, dev, stream, steps, warmup, storage="bf16", graphs_in_batch=512):
     """512 Watts-Strogatz graphs in one batched handle, R = 16, k = 15, 16-bit storage,
     per-graph 25% global per-node sparsification; against the plain FP32 form with
-    one handle per graph."""
+    one handle per graph.  graphs_in_batch < 512 takes the first graphs of the same
+    batch (a smaller case of the same kernels, e.g. for a profiler)."""
     import torch
     from paper_1601_05527_gb300 import graphgen
     st = storage if storage != "fp32" else "bf16"
-    graphs = graphgen.ws_batch(512, seed=5)
+    graphs = graphgen.ws_batch(512, seed=5)[:graphs_in_batch]
     voff, big = graphgen.concat(graphs)
     h = L.ad_graph_create_batched(voff, big.n, torch.from_numpy(big.row_ptr).to(dev),
                                   torch.from_numpy(big.col).to(dev), None, 0, stream)
@@ -502,8 +503,8 @@ def workload_ws512(L, dev, stream, steps, warmup, storage="bf16"):
     for hh in hs:
         L.ad_graph_destroy(hh)
     units = big.nnz * 16 * 15
-    return {"workload": "512 Watts-Strogatz graphs, n ~ U{1000..200000}, ring degree 10, p=0.1, R=16, k=15, "
-                        "per-graph 25% global per-node sparsification, one batched handle",
+    return {"workload": f"{len(graphs)} Watts-Strogatz graphs, n ~ U{{1000..200000}}, ring degree 10, p=0.1, R=16, "
+                        "k=15, per-graph 25% global per-node sparsification, one batched handle",
             "n": big.n, "m": big.m, "nnz": big.nnz, "storage": st, "value": units / (ms / 1e3), "unit": UNIT,
             "ms_per_step": ms,
             "roofline": _roofline(sweep_bytes(big.n, big.nnz, big.n, 16, 2, False), sw,
@@ -595,6 +596,8 @@ def run_workload(args):
     torch.cuda.set_stream(stream)
     fn = WORKLOADS[args.workload]
     kw = {} if args.workload in ("grid64", "rmat22") else {"storage": args.storage}
+    if args.workload == "ws512":
+        kw["graphs_in_batch"] = args.batch_graphs
     res = fn(L, dev, stream, args.steps, args.warmup, **kw)
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
@@ -612,6 +615,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16", "q16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=512,
+                    help="ws512 workload: run the first N graphs of the 512-graph batch (a smaller profiling case)")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the 16-bit storage comparison")
     ap.add_argument("--workload", default="rmat20", choices=["rmat20", "grid64", "ws512", "ba2m", "rmat22"],

@@ -264,14 +264,12 @@ __global__ void k_rank_count(const int64_t *rp, const int64_t *rows, int64_t nro
         if (live) { i = rows[t]; p0 = rp[i]; d = (int)(rp[i + 1] - p0); }
         const uint32_t k = gl < d ? ekey[p0 + gl] : 0xffffffffu;
         uint32_t r = 0, lt = 0, leq = 0;
-#pragma unroll
-        for (int l = 0; l < GS; ++l) {
+        // d is the same on every lane of the group, so the group's shuffles stay in step
+        for (int l = 0; l < d; ++l) {
             const uint32_t o = __shfl_sync(gmask, k, l, GS);
-            if (l < d) {
-                r += (o < k || (o == k && l < gl)) ? 1u : 0u;
-                lt += o < k ? 1u : 0u;
-                leq += o <= k ? 1u : 0u;
-            }
+            r += (o < k || (o == k && l < gl)) ? 1u : 0u;
+            lt += o < k ? 1u : 0u;
+            leq += o <= k ? 1u : 0u;
         }
         if (gl < d) put_ranks(out, p0 + gl, d, r, lt, leq);
     }
@@ -558,14 +556,14 @@ __global__ void k_info(const int64_t *epos, const int64_t *mirror, const int32_t
     }
 }
 
-// rank class of every row: 0 none, 1 d <= 8, 2 d <= 32, 3 d <= 64, 4 d <= 128, 5 d <= 256, 6 d <= 512,
-// 7 d <= kSortCap, 8 larger
-constexpr int kRankClasses = 9;
+// rank class of every row: 0 none, 1 d <= 8, 2 d <= 16, 3 d <= 32, 4 d <= 64, 5 d <= 128, 6 d <= 256,
+// 7 d <= 512, 8 d <= kSortCap, 9 larger
+constexpr int kRankClasses = 10;
 __global__ void k_rank_classes(const int64_t *rp, int64_t n, int8_t *cls /* class - 1; -1 for degree 0 */) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = rp[i + 1] - rp[i];
-        const int c = d == 0 ? 0 : d <= 8 ? 1 : d <= 32 ? 2 : d <= 64 ? 3 : d <= 128 ? 4 : d <= 256 ? 5 : d <= 512 ? 6
-                    : d <= kSortCap ? 7 : 8;
+        const int c = d == 0 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= 64 ? 4 : d <= 128 ? 5 : d <= 256 ? 6
+                    : d <= 512 ? 7 : d <= kSortCap ? 8 : 9;
         cls[i] = (int8_t)(c - 1);
     }
 }
@@ -586,6 +584,23 @@ __device__ __forceinline__ int graph_of_edge(const int64_t *goff_e, int G, int64
     return lo;
 }
 
+// The same for the edges of a whole warp (all 32 lanes call it; e < 0: no
+// edge): the graph of the first lane with an edge is looked up once and
+// checked by every lane, since a warp's edges mostly lie in one graph; lanes
+// outside it search on their own.
+__device__ __forceinline__ int graph_of_edge_warp(const int64_t *goff_e, int G, int64_t e) {
+    const unsigned have = __ballot_sync(0xffffffffu, e >= 0);
+    if (!have) return 0;
+    const int src = __ffs(have) - 1;
+    const int64_t e0 = __shfl_sync(0xffffffffu, e, src);
+    int g0 = 0;
+    if ((threadIdx.x & 31) == src) g0 = graph_of_edge(goff_e, G, e0);
+    g0 = __shfl_sync(0xffffffffu, g0, src);
+    if (e < 0) return 0;
+    if (__ldg(goff_e + g0) <= e && e < __ldg(goff_e + g0 + 1)) return g0;
+    return graph_of_edge(goff_e, G, e);
+}
+
 constexpr int kSharedFitProblems = 8;   // problems whose histograms a block keeps in shared memory
 __global__ void k_count_cand(const int4 *info, const int64_t *list, int64_t L, const int64_t *Ld, const int64_t *goff_e,
                              int G, const int32_t *T, int32_t ndc, int nc, unsigned long long *hist, uint8_t *cstar) {
@@ -601,9 +616,9 @@ __global__ void k_count_cand(const int4 *info, const int64_t *list, int64_t L, c
         const int64_t t = base + lane;
         int lo = 32;       // bin of a lane without an edge: never counted
         int gph = 0;
+        const int64_t e = t < L ? (list ? list[t] : t) : -1;
+        if (G > 1) gph = graph_of_edge_warp(goff_e, G, e);
         if (t < L) {
-            const int64_t e = list ? list[t] : t;
-            gph = G > 1 ? graph_of_edge(goff_e, G, e) : 0;
             const int4 f = info[e];
             const int32_t *Tg = T + (size_t)gph * nc * ndc;
             int l = 0, hi = nc;   // first candidate index (0-based) at which the edge is kept; nc = none
@@ -615,13 +630,12 @@ __global__ void k_count_cand(const int4 *info, const int64_t *list, int64_t L, c
             cstar[t] = (uint8_t)l;
             lo = l;
         }
-        if (shared_h) {
-            // lanes with the same (problem, bin) add once (few bins: shared-memory atomics would serialise)
-            const int key = lo < 32 ? gph * 32 + lo : -1;
-            const unsigned peers = __match_any_sync(0xffffffffu, key);
-            if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[key], (unsigned)__popc(peers));
-        } else if (lo < 32) {
-            atomicAdd(hist + (size_t)gph * 32 + lo, 1ull);
+        // lanes with the same (problem, bin) add once (few bins: per-lane atomics would serialise)
+        const int key = lo < 32 ? gph * 32 + lo : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) {
+            if (shared_h) atomicAdd(&h[key], (unsigned)__popc(peers));
+            else atomicAdd(hist + key, (unsigned long long)__popc(peers));
         }
     }
     __syncthreads();
@@ -785,13 +799,10 @@ __global__ void __launch_bounds__(256) k_fit_compact(const int64_t *list, int64_
 #pragma unroll
         for (int u = 0; u < kCompactItems; ++u) {
             const int64_t t = t0 + (int64_t)u * blockDim.x + threadIdx.x;
-            take[u] = false;
-            ev[u] = 0;
-            if (t < L) {
-                ev[u] = list ? list[t] : t;
-                const int gph = G > 1 ? graph_of_edge(goff_e, G, ev[u]) : 0;
-                take[u] = (int)cstar[t] == st[gph].jsel;
-            }
+            const int64_t e = t < L ? (list ? list[t] : t) : -1;
+            const int gph = G > 1 ? graph_of_edge_warp(goff_e, G, e) : 0;
+            take[u] = t < L && (int)cstar[t] == st[gph].jsel;
+            ev[u] = t < L ? e : 0;
             mine += take[u] ? 1u : 0u;
         }
         // exclusive prefix of `mine` over the block: warp scan, then warp totals
@@ -852,10 +863,10 @@ struct ad_graph_s::SelCache {
     ad::Tiles tiles;
     bool have_tiles = false;
     bool have_lists = false;
-    int64_t *rows[8] = {};          // rows of rank classes 1..8
-    int64_t nrows[8] = {};
-    int64_t *bstart = nullptr;      // class 8: first sorted slot of each row (nrows[7] + 1)
-    int64_t *bpos = nullptr;        // class 8 entries: CSR position and row slot
+    int64_t *rows[9] = {};          // rows of rank classes 1..9
+    int64_t nrows[9] = {};
+    int64_t *bstart = nullptr;      // class 9: first sorted slot of each row (nrows[8] + 1)
+    int64_t *bpos = nullptr;        // class 9 entries: CSR position and row slot
     int32_t *bseg = nullptr;
     int64_t nb_entries = 0;
     ad::DevBuf info, ekey, skey, bvals, T, hist, list_a, list_b, cstar, flag, jsel, kept, st, hist3, ties,
@@ -995,26 +1006,29 @@ static ad_status entry_ranks(ad_graph_t g, ad_graph_s::SelCache *c, const uint32
         AD_LAUNCH(k_rank_count<8>, wblocks(nr[0], 4), 256, 0, g->stream, g->rp, rows[0],
                   nr[0], ekey, out);
     if (nr[1] > 0)
-        AD_LAUNCH(k_rank_count<32>, wblocks(nr[1], 1), 256, 0, g->stream, g->rp, rows[1],
+        AD_LAUNCH(k_rank_count<16>, wblocks(nr[1], 2), 256, 0, g->stream, g->rp, rows[1],
                   nr[1], ekey, out);
     if (nr[2] > 0)
-        AD_LAUNCH(k_rank_wsort<2>, wblocks(nr[2], 1), 256, 0, g->stream, g->rp, rows[2],
+        AD_LAUNCH(k_rank_count<32>, wblocks(nr[2], 1), 256, 0, g->stream, g->rp, rows[2],
                   nr[2], ekey, out);
     if (nr[3] > 0)
-        AD_LAUNCH(k_rank_wsort<4>, wblocks(nr[3], 1), 256, 0, g->stream, g->rp, rows[3],
+        AD_LAUNCH(k_rank_wsort<2>, wblocks(nr[3], 1), 256, 0, g->stream, g->rp, rows[3],
                   nr[3], ekey, out);
     if (nr[4] > 0)
-        AD_LAUNCH(k_rank_wsort<8>, wblocks(nr[4], 1), 256, 0, g->stream, g->rp, rows[4],
+        AD_LAUNCH(k_rank_wsort<4>, wblocks(nr[4], 1), 256, 0, g->stream, g->rp, rows[4],
                   nr[4], ekey, out);
     if (nr[5] > 0)
-        AD_LAUNCH(k_rank_wsort<16>, wblocks(nr[5], 1), 256, 0, g->stream, g->rp, rows[5],
+        AD_LAUNCH(k_rank_wsort<8>, wblocks(nr[5], 1), 256, 0, g->stream, g->rp, rows[5],
                   nr[5], ekey, out);
-    if (nr[6] > 0) {
+    if (nr[6] > 0)
+        AD_LAUNCH(k_rank_wsort<16>, wblocks(nr[6], 1), 256, 0, g->stream, g->rp, rows[6],
+                  nr[6], ekey, out);
+    if (nr[7] > 0) {
         AD_TRY(set_mid_smem());
-        AD_LAUNCH(k_rank_mid, (int)nr[6], kMidThreads, kMidSmem, g->stream, g->rp, rows[6], ekey, out);
+        AD_LAUNCH(k_rank_mid, (int)nr[7], kMidThreads, kMidSmem, g->stream, g->rp, rows[7], ekey, out);
     }
     if (c->nb_entries > 0) {
-        const int64_t nb = c->nb_entries, nbig = nr[7];
+        const int64_t nb = c->nb_entries, nbig = nr[8];
         AD_TRY(ensure(g, c->skey, sizeof(uint64_t) * nb));
         AD_TRY(ensure(g, c->bvals, sizeof(int64_t) * nb));
         uint64_t *keys = static_cast<uint64_t *>(c->skey.ptr);

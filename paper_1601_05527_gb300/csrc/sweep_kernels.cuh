@@ -100,6 +100,21 @@ __device__ __forceinline__ int graph_of(const int64_t *voff, int G, int64_t row)
     return lo;
 }
 
+// graph_of with the vertex range of the last graph found kept: the rows a
+// lane group visits in a batch mostly lie in one graph, so most lookups are
+// one comparison instead of a binary search
+struct GraphCache {
+    int64_t lo = 0, hi = -1;
+    int g = 0;
+    __device__ __forceinline__ int of(const int64_t *voff, int G, int64_t row) {
+        if (row >= lo && row < hi) return g;
+        g = graph_of(voff, G, row);
+        lo = __ldg(voff + g);
+        hi = __ldg(voff + g + 1);
+        return g;
+    }
+};
+
 // task index range of warp `wid` among `W` warps: [t, t_end) stepping `step`
 struct TaskIter {
     int64_t t, t_end, step;
@@ -107,10 +122,15 @@ struct TaskIter {
 __device__ __forceinline__ TaskIter task_iter(int64_t n_tasks, int64_t wid, int64_t W, int blocked) {
     TaskIter it;
     if (blocked) {
-        const int64_t per = (n_tasks + W - 1) / W;
-        it.t = wid * per;
-        it.t_end = min(n_tasks, it.t + per);
-        it.step = 1;
+        // a contiguous range of tasks per CTA, the CTA's warps interleaved inside
+        // it: a batch's lanes then meet few graphs (each change of graph flushes
+        // the lane's min/max), and the CTA's warps share neighbouring rows
+        const int nw = blockDim.x >> 5;
+        const int64_t ncta = W / nw, cta = wid / nw;
+        const int64_t per = (n_tasks + ncta - 1) / ncta;
+        it.t = cta * per + wid % nw;
+        it.t_end = min(n_tasks, cta * per + per);
+        it.step = nw;
     } else {
         it.t = wid;
         it.t_end = n_tasks;
@@ -505,7 +525,8 @@ __device__ __forceinline__ void sweep_tasks(const SweepArgs &a, float *sm, const
     LaneStats<T, LPR, CPL> ls;
     ls.enter(a, gl, 0, false);
     if (P) ls.acg = acs;
-    auto row_graph = [&](int64_t row) { return a.G > 1 ? graph_of(a.voff, a.G, row) : 0; };
+    GraphCache gcache;
+    auto row_graph = [&](int64_t row) { return a.G > 1 ? gcache.of(a.voff, a.G, row) : 0; };
 
     const int64_t W = (int64_t)gridDim.x * nwarps;
     const TaskIter it = task_iter(a.n_tasks, (int64_t)blockIdx.x * nwarps + warp, W, a.blocked);
@@ -761,7 +782,8 @@ __device__ __forceinline__ void distance_tasks(const SweepArgs &a) {
                 A2[c * V + e] = (r < a.R) ? A[c * V + e] * A[c * V + e] : 0.f;
             }
     };
-    auto row_graph = [&](int64_t row) { return a.G > 1 ? graph_of(a.voff, a.G, row) : 0; };
+    GraphCache gcache;
+    auto row_graph = [&](int64_t row) { return a.G > 1 ? gcache.of(a.voff, a.G, row) : 0; };
     const int64_t W = (int64_t)gridDim.x * nwarps;
     const TaskIter it = task_iter(a.n_tasks, (int64_t)blockIdx.x * nwarps + warp, W, a.blocked);
     for (int64_t task = it.t; task < it.t_end; task += it.step) {

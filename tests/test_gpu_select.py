@@ -86,11 +86,12 @@ def test_per_node_at_exponent_bit_exact(mode, e):
 
 
 def boundary_graph(seed=8):
-    """Hubs of degree 512, 513, 1024, 4095, 4096 and 4097 -- the edges of the
-    per-row ranking classes (warp sort, CTA sort in shared memory, radix sort
-    of whole rows) -- over a sparse random background that avoids them."""
+    """Rows of degree 8, 9, 16, 17, 32, 33, 512, 513, 1024, 4095, 4096 and 4097
+    -- the edges of the per-row ranking classes (lane-group counting by 8, 16
+    and 32 lanes, warp sort, CTA sort in shared memory, radix sort of whole
+    rows) -- over a sparse random background that avoids them."""
     rng = np.random.default_rng(seed)
-    degs = (512, 513, 1024, 4095, 4096, 4097)
+    degs = (8, 9, 16, 17, 32, 33, 512, 513, 1024, 4095, 4096, 4097)
     H, n = len(degs), 20000
     u = [rng.integers(H, n, 30000)]
     v = [rng.integers(H, n, 30000)]
