@@ -246,6 +246,7 @@ __device__ __forceinline__ void put_ranks(const RankOut &o, int64_t p, int d, ui
 }
 
 constexpr int kSortCap = 4096;      // rows up to this degree are sorted by one CTA in shared memory
+constexpr int kSortCapLarge = 12288; // ... and up to this one by one CTA holding most of an SM's shared memory
 
 // rows of degree <= GS (8 or 32): a group of GS lanes per row, one entry per
 // lane, rank = number of smaller (key, position) pairs in the row
@@ -379,7 +380,8 @@ __device__ __forceinline__ int lower_bound_smem(const unsigned long long *a, int
     return lo;
 }
 
-// Rows of degree in (512, kSortCap]: one CTA per row sorts (key << 32 |
+// Rows of degree in (512, CAP] (CAP = kSortCap, or kSortCapLarge for the rows
+// above kSortCap): one CTA per row sorts (key << 32 |
 // position) with a stable LSD radix sort in shared memory (8-bit digits; a
 // digit pass whose keys all share one digit is skipped).  Each warp owns a
 // contiguous segment of whole 32-entry chunks.  Digit counts are shared-memory
@@ -388,13 +390,15 @@ __device__ __forceinline__ int lower_bound_smem(const unsigned long long *a, int
 // ballot per digit bit), so every pass is stable.  Four barriers per pass.
 constexpr int kMidThreads = 256, kMidWarps = kMidThreads / 32;
 static_assert(kMidThreads == 256, "one thread per 8-bit digit");
-constexpr size_t kMidSmem = 2 * kSortCap * sizeof(unsigned long long) + kMidWarps * 256 * sizeof(uint32_t);
+constexpr size_t mid_smem(int cap) { return 2 * (size_t)cap * sizeof(unsigned long long) + kMidWarps * 256 * sizeof(uint32_t); }
+static_assert(mid_smem(kSortCapLarge) <= 227 * 1024, "the large CTA sort must fit one CTA's shared memory");
 
+template <int CAP>
 __global__ void __launch_bounds__(kMidThreads) k_rank_mid(const int64_t *rp, const int64_t *rows, const uint32_t *ekey,
                                                           RankOut out) {
     extern __shared__ unsigned long long mid_sm[];
-    unsigned long long *a = mid_sm, *b = mid_sm + kSortCap;
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(mid_sm + 2 * kSortCap);   // [warp][256] counts, then offsets
+    unsigned long long *a = mid_sm, *b = mid_sm + CAP;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(mid_sm + 2 * CAP);   // [warp][256] counts, then offsets
     __shared__ uint32_t wsum[kMidWarps];                                    // digit totals of 32-digit blocks
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t row = rows[blockIdx.x];
@@ -473,13 +477,16 @@ static ad_status set_mid_smem() {
     std::lock_guard<std::mutex> lk(mu);
     if (dev < 0 || dev >= 64) return fail(AD_ERR_CUDA, "device index out of range");
     if (!done[dev]) {
-        AD_CUDA_TRY(cudaFuncSetAttribute(k_rank_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmem));
+        AD_CUDA_TRY(cudaFuncSetAttribute(k_rank_mid<kSortCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mid_smem(kSortCap)));
+        AD_CUDA_TRY(cudaFuncSetAttribute(k_rank_mid<kSortCapLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mid_smem(kSortCapLarge)));
         done[dev] = true;
     }
     return AD_OK;
 }
 
-// Rows of degree > kSortCap.  Their entries are listed once per handle
+// Rows of degree > kSortCapLarge.  Their entries are listed once per handle
 // (position bpos and row slot bseg, row slots in bstart order); each call sorts
 // (row slot, key) with the stable radix sort, whose input order is by position
 // inside a row, so each row's entries end up in (key, position) order.
@@ -557,13 +564,13 @@ __global__ void k_info(const int64_t *epos, const int64_t *mirror, const int32_t
 }
 
 // rank class of every row: 0 none, 1 d <= 8, 2 d <= 16, 3 d <= 32, 4 d <= 64, 5 d <= 128, 6 d <= 256,
-// 7 d <= 512, 8 d <= kSortCap, 9 larger
-constexpr int kRankClasses = 10;
+// 7 d <= 512, 8 d <= kSortCap, 9 d <= kSortCapLarge, 10 larger
+constexpr int kRankClasses = 11;
 __global__ void k_rank_classes(const int64_t *rp, int64_t n, int8_t *cls /* class - 1; -1 for degree 0 */) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = rp[i + 1] - rp[i];
         const int c = d == 0 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= 64 ? 4 : d <= 128 ? 5 : d <= 256 ? 6
-                    : d <= 512 ? 7 : d <= kSortCap ? 8 : 9;
+                    : d <= 512 ? 7 : d <= kSortCap ? 8 : d <= kSortCapLarge ? 9 : 10;
         cls[i] = (int8_t)(c - 1);
     }
 }
@@ -863,10 +870,10 @@ struct ad_graph_s::SelCache {
     ad::Tiles tiles;
     bool have_tiles = false;
     bool have_lists = false;
-    int64_t *rows[9] = {};          // rows of rank classes 1..9
-    int64_t nrows[9] = {};
-    int64_t *bstart = nullptr;      // class 9: first sorted slot of each row (nrows[8] + 1)
-    int64_t *bpos = nullptr;        // class 9 entries: CSR position and row slot
+    int64_t *rows[10] = {};         // rows of rank classes 1..10
+    int64_t nrows[10] = {};
+    int64_t *bstart = nullptr;      // class 10: first sorted slot of each row (nrows[9] + 1)
+    int64_t *bpos = nullptr;        // class 10 entries: CSR position and row slot
     int32_t *bseg = nullptr;
     int64_t nb_entries = 0;
     ad::DevBuf info, ekey, skey, bvals, T, hist, list_a, list_b, cstar, flag, jsel, kept, st, hist3, ties,
@@ -1023,12 +1030,15 @@ static ad_status entry_ranks(ad_graph_t g, ad_graph_s::SelCache *c, const uint32
     if (nr[6] > 0)
         AD_LAUNCH(k_rank_wsort<16>, wblocks(nr[6], 1), 256, 0, g->stream, g->rp, rows[6],
                   nr[6], ekey, out);
-    if (nr[7] > 0) {
-        AD_TRY(set_mid_smem());
-        AD_LAUNCH(k_rank_mid, (int)nr[7], kMidThreads, kMidSmem, g->stream, g->rp, rows[7], ekey, out);
-    }
+    if (nr[7] > 0 || nr[8] > 0) AD_TRY(set_mid_smem());
+    if (nr[7] > 0)
+        AD_LAUNCH(k_rank_mid<kSortCap>, (int)nr[7], kMidThreads, mid_smem(kSortCap), g->stream, g->rp, rows[7], ekey,
+                  out);
+    if (nr[8] > 0)
+        AD_LAUNCH(k_rank_mid<kSortCapLarge>, (int)nr[8], kMidThreads, mid_smem(kSortCapLarge), g->stream, g->rp,
+                  rows[8], ekey, out);
     if (c->nb_entries > 0) {
-        const int64_t nb = c->nb_entries, nbig = nr[8];
+        const int64_t nb = c->nb_entries, nbig = nr[9];
         AD_TRY(ensure(g, c->skey, sizeof(uint64_t) * nb));
         AD_TRY(ensure(g, c->bvals, sizeof(int64_t) * nb));
         uint64_t *keys = static_cast<uint64_t *>(c->skey.ptr);
@@ -1064,9 +1074,9 @@ ad_status long_rows(ad_graph_t g, const int64_t **rows, int64_t *count) {
     ad_graph_s::SelCache *c = nullptr;
     AD_TRY(sel_cache(g, &c));
     AD_TRY(rank_lists(g, c));
-    constexpr int NC = kRankClasses - 1;   // classes NC-2 and NC-1 (degree > 512) are adjacent in one array
-    *rows = c->rows[NC - 2];
-    *count = c->nrows[NC - 2] + c->nrows[NC - 1];
+    constexpr int NC = kRankClasses - 1;   // classes NC-3 .. NC-1 (degree > 512) are adjacent in one array
+    *rows = c->rows[NC - 3];
+    *count = c->nrows[NC - 3] + c->nrows[NC - 2] + c->nrows[NC - 1];
     return AD_OK;
 }
 

@@ -18,7 +18,7 @@ SEL_GRAPHS = {
     "ba2000": lambda: graphgen.barabasi_albert(2000, 6, seed=2),
     "grid32": lambda: graphgen.grid2d(32, 32),
     "rmat14": lambda: graphgen.rmat(14, 16, seed=5),
-    "hubs": lambda: hub_graph(),                           # rows of degree > 4096 (radix-sorted ranks)
+    "hubs": lambda: hub_graph(),                           # rows of degree 4500..9000 (the large CTA sort)
 }
 
 
@@ -86,12 +86,13 @@ def test_per_node_at_exponent_bit_exact(mode, e):
 
 
 def boundary_graph(seed=8):
-    """Rows of degree 8, 9, 16, 17, 32, 33, 512, 513, 1024, 4095, 4096 and 4097
-    -- the edges of the per-row ranking classes (lane-group counting by 8, 16
-    and 32 lanes, warp sort, CTA sort in shared memory, radix sort of whole
-    rows) -- over a sparse random background that avoids them."""
+    """Rows of degree 8, 9, 16, 17, 32, 33, 512, 513, 1024, 4095, 4096, 4097,
+    12288 and 12289 -- the edges of the per-row ranking classes (lane-group
+    counting by 8, 16 and 32 lanes, warp sort, CTA sorts in shared memory of
+    two sizes, radix sort of whole rows) -- over a sparse random background
+    that avoids them."""
     rng = np.random.default_rng(seed)
-    degs = (8, 9, 16, 17, 32, 33, 512, 513, 1024, 4095, 4096, 4097)
+    degs = (8, 9, 16, 17, 32, 33, 512, 513, 1024, 4095, 4096, 4097, 12288, 12289)
     H, n = len(degs), 20000
     u = [rng.integers(H, n, 30000)]
     v = [rng.integers(H, n, 30000)]
