@@ -299,10 +299,21 @@ __global__ void k_entry_rows(const int64_t *rp, int64_t n, int32_t *erow) {
     }
 }
 
-// one thread per entry: position of the reverse entry (binary search in row col[p])
+// Position of the reverse entry of every entry (mirror preset to -1): each
+// undirected pair is looked up once, by binary search in the shorter of its
+// two rows (equal lengths: from the larger row id), and both positions are
+// recorded.  An entry whose pair is missing (unvalidated asymmetric input)
+// keeps -1.
 __global__ void k_mirror(const int64_t *rp, const int32_t *col, const int32_t *erow, int64_t nnz, int64_t *mirror) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
-        mirror[p] = find_in_row(rp, col, col[p], erow[p]);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = erow[p], j = col[p];
+        const int64_t di = rp[i + 1] - rp[i], dj = rp[j + 1] - rp[j];
+        if (!(dj < di || (dj == di && j < i))) continue;     // the pair's other entry looks it up
+        const int64_t q = find_in_row(rp, col, j, i);
+        if (q < 0) continue;
+        mirror[p] = q;
+        mirror[q] = p;
+    }
 }
 
 // one thread per entry: the id of its edge (upper entries numbered row-major)
@@ -464,6 +475,7 @@ ad_status ensure_mirror(ad_graph_t g) {
         AD_TRY(dalloc_t(g, g->nnz, &g->mirror));
         const int64_t wblocks = std::min<int64_t>((g->n + 255) / 256 + 1, (int64_t)g->num_sms * 16);
         AD_LAUNCH(k_entry_rows, (int)wblocks, 256, 0, g->stream, g->rp, g->n, g->erow);
+        AD_CUDA_TRY(cudaMemsetAsync(g->mirror, 0xff, g->nnz * sizeof(int64_t), g->stream));
         AD_LAUNCH(k_mirror, grid, 256, 0, g->stream, g->rp, g->col, g->erow, g->nnz, g->mirror);
     }
     AD_TRY(dalloc_t(g, g->nnz, &g->eid));

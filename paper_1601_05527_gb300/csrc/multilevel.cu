@@ -54,12 +54,19 @@ __global__ void k_seed_init(const double *D, int64_t n, int8_t *state) {
 // they equal the sequential sums of the definition bit for bit.  On the other
 // rows a vertex waits until every predecessor is decided and then sums its
 // seed neighbours one after the other in CSR order, as the definition does.
+// One round over the vertices still undecided: list[0 .. *len) (list NULL: all
+// n vertices).  Vertices that stay undecided are appended to next[]
+// (*next_len counts them); their order there does not matter, since a
+// decision depends only on the final states of the vertex's predecessors.
 __global__ void k_seed_round(const int64_t *rp, const int32_t *col, const float *w, const double *D,
-                             const uint8_t *dexact, int64_t n, double Q, int8_t *state, unsigned long long *undecided) {
+                             const uint8_t *dexact, const int64_t *list, const unsigned long long *len, int64_t n,
+                             double Q, int8_t *state, int64_t *next, unsigned long long *next_len) {
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t L = list ? (int64_t)*len : n;
     volatile int8_t *vs = state;
-    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += W) {
+    for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < L; t += W) {
+        const int64_t i = list ? list[t] : t;
         if (vs[i] != S_UNDECIDED) continue;
         const double Di = D[i];
         const bool exact = !w || dexact[i];
@@ -83,12 +90,13 @@ __global__ void k_seed_round(const int64_t *rp, const int32_t *col, const float 
         und_any = __any_sync(0xffffffffu, und_any);
         if (lane == 0) {
             const double lim = Q * Di;
+            bool waiting = false;
             if (exact) {
                 if (seed_w > lim) vs[i] = S_F;
                 else if (seed_w + und_w <= lim) vs[i] = S_SEED;
-                else atomicAdd(undecided, 1ull);
+                else waiting = true;
             } else if (und_any) {
-                atomicAdd(undecided, 1ull);
+                waiting = true;
             } else {
                 double s = 0.0;   // successors may already be decided: only predecessors count
                 for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
@@ -98,31 +106,42 @@ __global__ void k_seed_round(const int64_t *rp, const int32_t *col, const float 
                 }
                 vs[i] = s <= lim ? S_SEED : S_F;
             }
+            if (waiting) next[atomicAdd(next_len, 1ull)] = i;
         }
     }
 }
 
+// Rounds over the undecided vertices until none is left; the count is read
+// back every kSeedRoundsPerCheck rounds (a round on an empty list returns at once).
+constexpr int kSeedRoundsPerCheck = 4;
 static ad_status create_seeds(ad_graph_t g, double Q, int8_t *state) {
     const int64_t n = g->n;
     if (n == 0) return AD_OK;
     const int grid = g->num_sms * 8;
     AD_LAUNCH(k_seed_init, grid, 256, 0, g->stream, g->D, n, state);
-    unsigned long long *und = nullptr;
-    AD_TRY(dalloc_t(g, 1, &und));
+    int64_t *lists = nullptr;
+    unsigned long long *lens = nullptr;
+    AD_TRY(dalloc_t(g, 2 * (size_t)n, &lists));
+    AD_TRY(dalloc_t(g, 2, &lens));
+    auto release = [&]() {
+        dfree(g, lists);
+        dfree(g, lens);
+    };
     const int64_t wblocks = std::min<int64_t>((n + 7) / 8 + 1, (int64_t)g->num_sms * 32);
     for (int64_t round = 0;; ++round) {
-        if (round > n + 1) {
-            dfree(g, und);
+        if (round > n + kSeedRoundsPerCheck) {
+            release();
             return fail(AD_ERR_STATE, "seed selection did not converge");
         }
-        AD_CUDA_TRY(cudaMemsetAsync(und, 0, sizeof(unsigned long long), g->stream));
-        AD_LAUNCH(k_seed_round, (int)wblocks, 256, 0, g->stream, g->rp, g->col, g->w, g->D, g->dexact, n, Q, state,
-                  und);
-        unsigned long long u = 0;
-        AD_TRY(copy_out(g, &u, und, sizeof(u)));
+        const int a = (int)(round & 1), b = a ^ 1;
+        AD_CUDA_TRY(cudaMemsetAsync(lens + b, 0, sizeof(unsigned long long), g->stream));
+        AD_LAUNCH(k_seed_round, (int)wblocks, 256, 0, g->stream, g->rp, g->col, g->w, g->D, g->dexact,
+                  round == 0 ? nullptr : lists + (size_t)a * n, lens + a, n, Q, state, lists + (size_t)b * n, lens + b);
+        unsigned long long u = 1;
+        if ((round + 1) % kSeedRoundsPerCheck == 0) AD_TRY(copy_out(g, &u, lens + b, sizeof(u)));
         if (u == 0) break;
     }
-    dfree(g, und);
+    release();
     return AD_OK;
 }
 
@@ -212,13 +231,15 @@ __global__ void k_segment_sum(const uint64_t *key, const int64_t *fine, const in
     cw[s] = (float)sum;
 }
 
+// lanes with the same end add once (ca is sorted, so a warp mostly shares one)
 __global__ void k_count_ends(const int32_t *ca, const int32_t *cb, int64_t mc, unsigned long long *cnt_up,
                              unsigned long long *cnt_lo) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < mc) {
-        atomicAdd(cnt_up + ca[s], 1ull);
-        atomicAdd(cnt_lo + cb[s], 1ull);
-    }
+    const unsigned lower = (1u << (threadIdx.x & 31)) - 1u;
+    const int32_t a = s < mc ? ca[s] : -1, b = s < mc ? cb[s] : -1;
+    const unsigned pa = __match_any_sync(0xffffffffu, a), pb = __match_any_sync(0xffffffffu, b);
+    if (a >= 0 && (pa & lower) == 0) atomicAdd(cnt_up + a, (unsigned long long)__popc(pa));
+    if (b >= 0 && (pb & lower) == 0) atomicAdd(cnt_lo + b, (unsigned long long)__popc(pb));
 }
 
 __global__ void k_add_counts(const unsigned long long *a, const unsigned long long *b, int64_t n, int64_t *out) {
