@@ -743,7 +743,8 @@ __device__ __forceinline__ void edge_rows(const SweepArgs &a, int64_t row, int64
         int which = 0;
         group_sums<LPR, UB>(s, gl, gmask, which);
         constexpr int NH = UB / LPR > 0 ? UB / LPR : 1;
-        const bool writer = (LPR <= UB) || (gl % (LPR / UB) == 0);
+        constexpr int WS = LPR > UB ? LPR / UB : 1;   // lanes per edge that hold the same sum
+        const bool writer = gl % WS == 0;
 #pragma unroll
         for (int i = 0; i < NH; ++i) {
             int32_t jw = 0;

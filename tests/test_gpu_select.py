@@ -255,6 +255,47 @@ def test_cached_ranks_follow_the_distances():
     L.ad_graph_destroy(h)
 
 
+def test_ranking_follows_every_kind_of_distance_call():
+    """The handle's cached ranking of its own distances must follow each new
+    distance call -- run directly, replayed from a recorded CUDA graph, as the
+    persistent launch, with normalised scores -- and survive other rankings
+    in between (Local Degree's, a caller's scores).  Every selection must be
+    the oracle's on the distances of the call."""
+    import torch
+    L = lib()
+    g = graphgen.rmat(12, 16, seed=5)
+    st = torch.cuda.Stream()
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, None, 0, st)
+    rho = np.zeros(g.m, np.float32)
+    keep = np.zeros(g.m, np.uint8)
+
+    def check(mode):
+        kept, e = L.ad_sparsify(h, 0.3, mode, "per_node", keep)
+        ref, rk, re_ = oracle.sparsify(g.row_ptr, g.col, rho.astype(np.float64), mode, "per_node", 0.3)
+        assert e == re_ and kept == rk
+        np.testing.assert_array_equal(keep, ref)
+
+    calls = [(1, 0), (2, 0), (2, 0), (2, 0), (2, 0), (3, L.AD_DIST_PERSISTENT), (4, L.AD_DIST_NORMALIZE),
+             (4, L.AD_DIST_NORMALIZE), (5, 0)]
+    try:
+        for i, (seed, flags) in enumerate(calls):
+            L.ad_algebraic_distance(h, 16, 8, 0.5, seed, 0, "fp32", flags, rho)
+            check("local")
+            check("global")
+            if i == 3:
+                L.ad_sparsify_local_degree(h, 0.3, keep)
+            if i == 6:
+                L.ad_sparsify_scores(h, graphgen.random_scores(g.m, 25, seed=3), 0.3, "local", "per_node", keep)
+        kl, kg = np.zeros(g.m, np.uint8), np.zeros(g.m, np.uint8)
+        L.ad_algebraic_distance(h, 16, 8, 0.5, 6, 0, "fp32", 0, rho)
+        L.ad_sparsify_local_global(h, 0.3, kl, kg)
+        for mode, k in (("local", kl), ("global", kg)):
+            np.testing.assert_array_equal(k, oracle.sparsify(g.row_ptr, g.col, rho.astype(np.float64), mode,
+                                                             "per_node", 0.3)[0])
+    finally:
+        L.ad_graph_destroy(h)
+
+
 @pytest.mark.parametrize("name", ["rmat13", "hubs", "batch"])
 def test_local_and_global_in_one_call(name):
     """ad_sparsify_local_global (one ranking, one two-problem exponent search)
