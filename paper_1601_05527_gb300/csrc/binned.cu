@@ -20,11 +20,13 @@
 // proves it equal to the FP64 quotient's floor, and cbrt(d) comes from the
 // host's FP64 cbrt.
 //
-// Pipeline: per-row statistics (one warp per 32 rows), per-entry bin and
-// Philox word, per-row ranks by word and then by (bin, rank by word), runs of
-// equal (row, bin) = the non-empty bins, their order inside the row (counted
-// directly for rows of few bins), and per entry the round-robin rank, again a
-// per-row rank.
+// Pipeline: per-row statistics (one warp per 32 rows, one block per row above
+// 512 entries), per-entry bin and Philox word, one per-row rank by (bin, top
+// bits of the word) with the rare ties of the truncated word put in full-word
+// order afterwards, runs of equal (row, bin) = the non-empty bins, their order
+// inside the row (counted directly for rows of few bins), and per entry the
+// round-robin rank (counted directly where that is cheaper than a per-row rank
+// pass).
 #include "ad_internal.cuh"
 
 #include <algorithm>
@@ -423,9 +425,44 @@ __global__ void k_bin_words(const int32_t *erow, const int64_t *eid, const float
     if ((threadIdx.x & 31) == 0 && mb) atomicMax(max_bin, mb);
 }
 
-__global__ void k_bin_key2(const uint32_t *bin, const uint32_t *rw, int64_t nnz, uint32_t *key) {
+// Key of the one per-row ranking pass: the bin in the top bbits bits, the top
+// 32 - bbits bits of the entry's Philox word below it.  Ranking by (key,
+// position) orders a row by (bin, word) except among entries of one bin whose
+// truncated words tie; k_bin_fix_ties puts those in (word, position) order.
+__global__ void k_bin_key1(const uint32_t *bin, const uint32_t *word, int64_t nnz, int bbits, uint32_t *key) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
-        key[p] = (bin[p] << kRowRankBits) | rw[p];
+        key[p] = bbits == 0 ? word[p] : (bin[p] << (32 - bbits)) | (word[p] >> bbits);
+}
+
+// Runs of equal key inside a row in the sorted slots: the first slot of each
+// run of two or more reorders it by (full word, position) -- an insertion sort,
+// the runs being short (two entries collide with probability 2^(bbits - 32)).
+__global__ void k_bin_fix_ties(int32_t *sorted, const int32_t *erow, const uint32_t *key, const uint32_t *word,
+                               int64_t nnz) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = sorted[s];
+        const int32_t row = erow[p];
+        const uint32_t k = key[p];
+        if (s > 0) {
+            const int32_t pp = sorted[s - 1];
+            if (erow[pp] == row && key[pp] == k) continue;     // not the first slot of its run
+        }
+        int64_t e = s + 1;
+        while (e < nnz && erow[sorted[e]] == row && key[sorted[e]] == k) ++e;
+        for (int64_t a = s + 1; a < e; ++a) {
+            const int32_t v = sorted[a];
+            const uint32_t wv = word[v];
+            int64_t b = a - 1;
+            while (b >= s) {
+                const int32_t u = sorted[b];
+                const uint32_t wu = word[u];
+                if (wu < wv || (wu == wv && u < v)) break;
+                sorted[b + 1] = u;
+                --b;
+            }
+            sorted[b + 1] = v;
+        }
+    }
 }
 
 // entries in (bin, word) order inside their rows: slot rp[row] + rank
@@ -548,7 +585,8 @@ ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint
     for (int32_t q = 0; q < g->n_deg_classes; ++q) cb[q] = std::cbrt((double)g->distinct_degrees[q]);
     double *cbrt_dc = nullptr, *h = nullptr;
     float *lo = nullptr, *xs = nullptr, *rinv = nullptr;
-    uint32_t *bin = nullptr, *key = nullptr, *rk = nullptr, *desc = nullptr, *sbin = nullptr, *order = nullptr;
+    uint32_t *bin = nullptr, *key = nullptr, *rk = nullptr, *desc = nullptr, *sbin = nullptr, *order = nullptr,
+             *tkey = nullptr;
     int32_t *sorted = nullptr;
     int64_t *flag = nullptr, *run_of = nullptr, *run_start = nullptr, *rval = nullptr, *row_runs = nullptr;
     uint64_t *rkey = nullptr;
@@ -580,7 +618,8 @@ ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint
     unsigned long long mb = 0;
     AD_TRY(copy_out(g, &mb, max_bin, sizeof(mb)));
     auto release = [&]() {
-        for (void *p : {(void *)cbrt_dc, (void *)lo, (void *)h, (void *)rinv, (void *)xs, (void *)bin, (void *)key, (void *)rk,
+        for (void *p : {(void *)cbrt_dc, (void *)lo, (void *)h, (void *)rinv, (void *)xs, (void *)bin, (void *)key,
+                        (void *)tkey, (void *)rk,
                         (void *)desc, (void *)max_bin, (void *)sbin, (void *)sorted, (void *)flag, (void *)run_of,
                         (void *)run_start, (void *)rval, (void *)row_runs, (void *)rkey, (void *)order})
             if (p) dfree(g, p);
@@ -590,14 +629,17 @@ ad_status binned_ranks(ad_graph_t g, const float *score_dev, uint64_t seed, uint
         return binned_ranks_sorted(g, score_dev, seed, rank_dev, bin_dev);
     }
     if (bin_dev) AD_CUDA_TRY(cudaMemcpyAsync(bin_dev, bin, nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, g->stream));
-    AD_TRY(row_ranks(g, key, rk, desc));                                   // 1. by word
-    AD_LAUNCH(k_bin_key2, big, 256, 0, g->stream, bin, rk, nnz, key);
-    AD_TRY(row_ranks(g, key, rk, desc));                                   // 2. by (bin, word)
+    int bbits = 0;                                                          // bits of the largest bin index
+    while (((unsigned long long)1 << bbits) <= mb) ++bbits;
+    AD_TRY(dalloc_t(g, nnz, &tkey));
+    AD_LAUNCH(k_bin_key1, big, 256, 0, g->stream, bin, key, nnz, bbits, tkey);
+    AD_TRY(row_ranks(g, tkey, rk, desc));                                  // 1. by (bin, word)
     AD_TRY(dalloc_t(g, nnz, &sorted));
     AD_TRY(dalloc_t(g, nnz, &sbin));
     AD_TRY(dalloc_t(g, nnz, &flag));
     AD_TRY(dalloc_t(g, nnz, &run_of));
     AD_LAUNCH(k_bin_place, big, 256, 0, g->stream, g->erow, g->rp, rk, bin, nnz, sorted, sbin);
+    if (bbits > 0) AD_LAUNCH(k_bin_fix_ties, big, 256, 0, g->stream, sorted, g->erow, tkey, key, nnz);
     AD_LAUNCH(k_bin_run_starts, big, 256, 0, g->stream, sorted, g->erow, sbin, nnz, flag);
     int64_t nruns = 0;
     AD_TRY(exclusive_scan_i64(g, flag, run_of, nnz, &nruns));
