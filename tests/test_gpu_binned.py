@@ -159,3 +159,26 @@ def test_binned_rows_of_many_bins():
         check_keep(L, h, g, s, 0.3, 5, flips)
     finally:
         L.ad_graph_destroy(h)
+
+
+def test_binned_ties_of_the_truncated_word():
+    """One far outlier stretches a hub row over ~1,100 bins (the key keeps only
+    the top 21 bits of each Philox word) while its other 19,999 distances share
+    bin 0, where about a hundred pairs of truncated words collide: the ranks
+    must still follow the full words, as the oracle's do."""
+    L = lib()
+    n = 20001
+    g = graphgen.from_edges(n, np.zeros(n - 1, np.int64), np.arange(1, n))
+    rng = np.random.default_rng(12)
+    s = (rng.random(g.m) * 1e-3).astype(np.float32)
+    s[rng.integers(0, g.m)] = 100.0
+    _, ref_bins = oracle.binned_ranks(g.row_ptr, g.col, s.astype(np.float64), 7, return_bins=True)
+    hub = ref_bins[:g.degrees()[0]]
+    assert 1024 <= hub.max() < 2048 and (hub == 0).sum() == g.m - 1     # the case this test is for
+    h = L.ad_graph_create(g.n, g.row_ptr, g.col, None)
+    try:
+        flips, _ = check_bins_and_ranks(L, h, g, s, 7)
+        assert flips == 0
+        check_keep(L, h, g, s, 0.3, 7, flips)
+    finally:
+        L.ad_graph_destroy(h)
